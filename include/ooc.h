@@ -1,0 +1,189 @@
+/*
+ * ooc.h — C ABI of the GB300 out-of-core GEMM library (libooc.so).
+ *
+ * The problem is the one stated in Section IV of the libhclooc paper
+ * (arXiv:1808.05056): C = alpha * A * B + beta * C with A of M x K, B of K x N
+ * and C of M x N, where the matrices live in host memory and together exceed
+ * the device memory the caller grants.  The library partitions A into
+ * horizontal slices, B into vertical slices and C into blocks (Section IV,
+ * partitioner paragraph and Fig. 2), streams them through a budget-sized set of
+ * device buffers (the five pipeline stages S(b_j), S(a_i), S(c_ij), GEMM,
+ * R(c_ij) of Section IV) and runs the per-block product with its own sm_103a
+ * kernels.
+ *
+ * Conventions for every call below
+ *   - Storage is row-major: element (r, c) of a stored matrix X with leading
+ *     dimension ldX is X[r * ldX + c].  trans is 'N' (op(X) = X) or 'T'
+ *     (op(X) = X^T); for transA == 'N' A is stored M x K (lda >= K), for 'T'
+ *     it is stored K x M (lda >= M); likewise B is K x N (ldb >= N) or N x K
+ *     (ldb >= K); C is M x N (ldc >= N).
+ *   - Host pointers must point to page-locked memory (cudaHostAlloc or
+ *     cudaHostRegister'ed by the caller): the call checks and returns
+ *     OOC_ERR_NOT_PINNED instead of staging through pageable memory.
+ *   - The caller owns every host buffer; the library never frees or keeps
+ *     them.  The call is synchronous: it returns when C is back on the host.
+ *   - beta == 0 never reads C (NaN in C is ignored); K == 0 gives C = beta*C;
+ *     M == 0 or N == 0 is a no-op returning OOC_OK.
+ *   - Device memory: at most device_budget_bytes are used for the operand
+ *     buffers.  If opts->workspace is non-NULL the buffers are carved from
+ *     that caller-owned device allocation (which must hold
+ *     device_budget_bytes) and nothing is allocated; otherwise one arena of
+ *     at most device_budget_bytes is allocated and freed before return.
+ *   - Errors: every call returns OOC_OK (0) or a negative OOC_ERR_* code and
+ *     never aborts the process.  ooc_strerror() names a code; ooc_last_error()
+ *     gives a one-line detail of the last failure on the calling thread.
+ */
+#ifndef OOC_H
+#define OOC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define OOC_OK 0
+#define OOC_ERR_INVALID_ARG (-1)    /* bad trans, dims, leading dimensions or options   */
+#define OOC_ERR_BUDGET (-2)         /* budget below the smallest plan for this problem  */
+#define OOC_ERR_NOT_PINNED (-3)     /* a host operand is not page-locked                */
+#define OOC_ERR_CUDA (-4)           /* a CUDA runtime/driver call failed                */
+#define OOC_ERR_NO_DEVICE (-5)      /* no usable sm_103 device                          */
+#define OOC_ERR_TIMEOUT (-6)        /* a bounded device-side wait gave up               */
+#define OOC_ERR_ALLOC (-7)          /* device arena allocation failed                   */
+#define OOC_ERR_UNSUPPORTED (-8)    /* form/option not available for this call          */
+#define OOC_ERR_INJECTED (-9)       /* failure injected by OOC_FAULT_INJECT (testing)   */
+#define OOC_ERR_CAPACITY (-10)      /* output array too small (schedule export)         */
+
+/* ---- contraction forms ----------------------------------------------- */
+#define OOC_FORM_AUTO 0    /* dgemm: FP64; sgemm: BF16x3                                 */
+#define OOC_FORM_FP64 1    /* plain FP64 tiles (FP64 tensor-core MMA)                    */
+#define OOC_FORM_OZAKI 2   /* FP64-accurate: Ozaki bf16 slice products, FP64 accumulate  */
+#define OOC_FORM_BF16X3 3  /* FP32-accurate: three-piece bf16 split, six products        */
+
+/* ---- plan selection flags (ooc_opts.flags) --------------------------- */
+#define OOC_PLAN_PAPER 1u  /* Section IV partitioner: equal h x w split, 2A + 1B + 2C buffers */
+
+/*
+ * Options; a zero-initialised struct means "choose automatically".
+ * mb, nb, kb: C block rows, C block columns and K-chunk length.
+ * depth: A-slice buffers (2 or 3); c_buffers: C-block buffers.
+ * slices: Ozaki slice count (0 = chosen from the input exponent spread).
+ * workspace/workspace_bytes: optional caller-owned device memory for the
+ * buffers (see the conventions above).
+ */
+typedef struct {
+    int32_t form;
+    int32_t depth;
+    int32_t c_buffers;
+    int32_t slices;
+    int64_t mb, nb, kb;
+    uint32_t flags;
+    uint32_t reserved;
+    void* workspace;
+    size_t workspace_bytes;
+} ooc_opts;
+
+/* What a call did; every field is filled on OOC_OK. */
+typedef struct {
+    double seconds;          /* host wall time of the call                          */
+    double device_seconds;   /* first H2D start to last D2H end (CUDA events)       */
+    double kernel_seconds;   /* summed duration of the tile-contraction launches    */
+    double tflops;           /* 2*M*N*K / seconds / 1e12 (transfers included)       */
+    double h2d_bytes;        /* bytes copied host -> device                          */
+    double d2h_bytes;        /* bytes copied device -> host                          */
+    int64_t mb, nb, kb;      /* plan used                                            */
+    int32_t depth, c_buffers, b_buffers, form;
+    int64_t blocks;          /* C blocks (h * w)                                     */
+    int64_t steps;           /* block x K-chunk steps (tile launches)                */
+    int64_t device_bytes;    /* device buffer bytes the plan uses                    */
+    int32_t slices;          /* Ozaki slices / BF16x3 pieces used                    */
+    int32_t products;        /* slice products per tile                              */
+} ooc_stats;
+
+/*
+ * Out-of-core DGEMM: C = alpha * op(A) * op(B) + beta * C, FP64 host
+ * operands (Section IV problem statement; per-block update c_ij =
+ * alpha a_i b_j + beta c_ij of the DGEMM stage).  opts->form selects plain
+ * FP64 tiles (default) or the FP64-accurate Ozaki form.  opts and stats may
+ * be NULL.
+ */
+int ooc_dgemm(char transA, char transB, int64_t M, int64_t N, int64_t K, double alpha,
+              const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
+              double* C, int64_t ldc, size_t device_budget_bytes, const ooc_opts* opts,
+              ooc_stats* stats);
+
+/*
+ * Out-of-core SGEMM with FP32-accurate BF16x3 tiles: FP32 host operands and
+ * result, the same problem statement as ooc_dgemm.  alpha and beta are
+ * applied in FP64 before the result is rounded to FP32.
+ */
+int ooc_sgemm(char transA, char transB, int64_t M, int64_t N, int64_t K, float alpha,
+              const float* A, int64_t lda, const float* B, int64_t ldb, float beta,
+              float* C, int64_t ldc, size_t device_budget_bytes, const ooc_opts* opts,
+              ooc_stats* stats);
+
+/*
+ * In-core device GEMM (the paper's runtime DGEMM call of the pipeline's
+ * compute stage): C = alpha * op(A) * op(B) + beta * C on device pointers,
+ * FP64, enqueued on `stream` (a cudaStream_t, NULL = legacy default stream)
+ * and not synchronised.  Same layout rules as ooc_dgemm; no allocation.
+ */
+int ooc_dgemm_device(char transA, char transB, int64_t M, int64_t N, int64_t K, double alpha,
+                     const double* dA, int64_t lda, const double* dB, int64_t ldb, double beta,
+                     double* dC, int64_t ldc, void* stream);
+
+/*
+ * Plan only (host, no device needed): the block/chunk/buffer plan the call
+ * with these arguments would use.  elem_bytes is 8 for ooc_dgemm, 4 for
+ * ooc_sgemm.  Fills stats' plan fields (mb, nb, kb, depth, c_buffers,
+ * b_buffers, form, blocks, steps, device_bytes, h2d_bytes, d2h_bytes).
+ * Section IV partitioner paragraph; worked example of Fig. 2.
+ */
+int ooc_plan(int64_t M, int64_t N, int64_t K, int32_t elem_bytes, int32_t beta_nonzero,
+             size_t device_budget_bytes, const ooc_opts* opts, ooc_stats* plan);
+
+/*
+ * One operation of an issued pipeline schedule (host issue order), for
+ * checking the Section IV buffer-hazard rule without a GPU.
+ * kind: 0 H2D copy, 1 tile kernel, 2 D2H copy, 3 event record, 4 event wait.
+ * stream: 0 H2D stream, 1 compute stream, 2 D2H stream.
+ * A tag names the datum in a device slot: {matrix (0 A, 1 B, 2 C),
+ * row chunk, column chunk, version}; a C block's version counts the K-chunks
+ * folded into it.  Unused slots are -1.
+ */
+typedef struct {
+    int32_t kind, stream, event, nreads;
+    int32_t write_slot;
+    int32_t read_slot[3];
+    int64_t write_tag[4];
+    int64_t read_tag[3][4];
+} ooc_sched_op;
+
+/*
+ * Export the schedule ooc_dgemm (elem_bytes 8) or ooc_sgemm (4) would issue.
+ * Writes at most capacity ops to out; *count receives the total.  Returns
+ * OOC_ERR_CAPACITY (with *count set) when out is too small.
+ */
+int ooc_schedule(int64_t M, int64_t N, int64_t K, int32_t elem_bytes, int32_t beta_nonzero,
+                 size_t device_budget_bytes, const ooc_opts* opts, ooc_sched_op* out,
+                 int64_t capacity, int64_t* count);
+
+/*
+ * hclGetMemSize analogue (Section III runtime methods): free device memory,
+ * and host-link bandwidth in GB/s measured once per process with pinned
+ * 256 MiB copies (H2D, D2H).  Any pointer may be NULL.
+ */
+int ooc_query_device(size_t* free_bytes, double* h2d_gbps, double* d2h_gbps);
+
+/* Name of a status code (static string). */
+const char* ooc_strerror(int code);
+
+/* One-line detail of the last failure on the calling thread (static per thread). */
+const char* ooc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OOC_H */

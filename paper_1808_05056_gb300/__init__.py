@@ -1,0 +1,241 @@
+"""Python binding of libooc, the GB300 out-of-core GEMM (C ABI in include/ooc.h).
+
+Every function here only marshals arguments into the C ABI of the same name;
+all work runs in the library's CUDA kernels and copy streams.  There is no
+CPU path: if the compiled library is missing, ``load()`` raises.
+
+Host operands must be page-locked (e.g. ``torch.empty(..., pin_memory=True)``);
+tensors are passed as row-major 2-D arrays whose rows are contiguous.
+"""
+import ctypes
+import os
+
+from . import _build
+
+LIB_PATH = _build.LIB
+
+OOC_OK = 0
+OOC_ERR_INVALID_ARG = -1
+OOC_ERR_BUDGET = -2
+OOC_ERR_NOT_PINNED = -3
+OOC_ERR_CUDA = -4
+OOC_ERR_NO_DEVICE = -5
+OOC_ERR_TIMEOUT = -6
+OOC_ERR_ALLOC = -7
+OOC_ERR_UNSUPPORTED = -8
+OOC_ERR_INJECTED = -9
+OOC_ERR_CAPACITY = -10
+
+OOC_FORM_AUTO, OOC_FORM_FP64, OOC_FORM_OZAKI, OOC_FORM_BF16X3 = 0, 1, 2, 3
+OOC_PLAN_PAPER = 1
+
+
+class ooc_opts(ctypes.Structure):
+    _fields_ = [("form", ctypes.c_int32), ("depth", ctypes.c_int32), ("c_buffers", ctypes.c_int32),
+                ("slices", ctypes.c_int32), ("mb", ctypes.c_int64), ("nb", ctypes.c_int64),
+                ("kb", ctypes.c_int64), ("flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t)]
+
+
+class ooc_stats(ctypes.Structure):
+    _fields_ = [("seconds", ctypes.c_double), ("device_seconds", ctypes.c_double),
+                ("kernel_seconds", ctypes.c_double), ("tflops", ctypes.c_double),
+                ("h2d_bytes", ctypes.c_double), ("d2h_bytes", ctypes.c_double),
+                ("mb", ctypes.c_int64), ("nb", ctypes.c_int64), ("kb", ctypes.c_int64),
+                ("depth", ctypes.c_int32), ("c_buffers", ctypes.c_int32), ("b_buffers", ctypes.c_int32),
+                ("form", ctypes.c_int32), ("blocks", ctypes.c_int64), ("steps", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64), ("slices", ctypes.c_int32), ("products", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ooc_sched_op(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("stream", ctypes.c_int32), ("event", ctypes.c_int32),
+                ("nreads", ctypes.c_int32), ("write_slot", ctypes.c_int32),
+                ("read_slot", ctypes.c_int32 * 3), ("write_tag", ctypes.c_int64 * 4),
+                ("read_tag", (ctypes.c_int64 * 4) * 3)]
+
+
+EXPORTS = ("ooc_dgemm", "ooc_sgemm", "ooc_dgemm_device", "ooc_plan", "ooc_schedule",
+           "ooc_query_device", "ooc_strerror", "ooc_last_error")
+
+_lib = None
+
+
+class OocError(RuntimeError):
+    def __init__(self, code, fn):
+        self.code = code
+        lib = load()
+        super().__init__("%s: %s (%d): %s" % (fn, lib.ooc_strerror(code).decode(), code,
+                                              lib.ooc_last_error().decode()))
+
+
+def build(force=False):
+    """Compile libooc.so for sm_103a (in-tree)."""
+    return _build.build(force=force)
+
+
+def load(path=None):
+    """Load libooc.so and declare its signatures; raises if it is not built."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError("libooc.so is not built (%s); run paper_1808_05056_gb300.build()" % p)
+    lib = ctypes.CDLL(p)
+    i64, i32, dbl, flt, vp, ch = (ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_float,
+                                  ctypes.c_void_p, ctypes.c_char)
+    sz = ctypes.c_size_t
+    po, ps = ctypes.POINTER(ooc_opts), ctypes.POINTER(ooc_stats)
+    lib.ooc_dgemm.argtypes = [ch, ch, i64, i64, i64, dbl, vp, i64, vp, i64, dbl, vp, i64, sz, po, ps]
+    lib.ooc_sgemm.argtypes = [ch, ch, i64, i64, i64, flt, vp, i64, vp, i64, flt, vp, i64, sz, po, ps]
+    lib.ooc_dgemm_device.argtypes = [ch, ch, i64, i64, i64, dbl, vp, i64, vp, i64, dbl, vp, i64, vp]
+    lib.ooc_plan.argtypes = [i64, i64, i64, i32, i32, sz, po, ps]
+    lib.ooc_schedule.argtypes = [i64, i64, i64, i32, i32, sz, po, ctypes.POINTER(ooc_sched_op), i64,
+                                 ctypes.POINTER(i64)]
+    lib.ooc_query_device.argtypes = [ctypes.POINTER(sz), ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
+    lib.ooc_strerror.argtypes = [ctypes.c_int]
+    lib.ooc_strerror.restype = ctypes.c_char_p
+    lib.ooc_last_error.argtypes = []
+    lib.ooc_last_error.restype = ctypes.c_char_p
+    for f in ("ooc_dgemm", "ooc_sgemm", "ooc_dgemm_device", "ooc_plan", "ooc_schedule", "ooc_query_device"):
+        getattr(lib, f).restype = ctypes.c_int
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _opts(form=0, depth=0, c_buffers=0, slices=0, mb=0, nb=0, kb=0, flags=0, workspace=None,
+          workspace_bytes=0):
+    o = ooc_opts()
+    o.form, o.depth, o.c_buffers, o.slices = form, depth, c_buffers, slices
+    o.mb, o.nb, o.kb, o.flags = mb, nb, kb, flags
+    o.workspace = workspace
+    o.workspace_bytes = workspace_bytes
+    return o
+
+
+def make_opts(**kw):
+    """An ooc_opts with the given fields (the rest zero = automatic)."""
+    return _opts(**kw)
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    return x.ctypes.data
+
+
+def _ld(x):
+    if hasattr(x, "stride"):
+        return x.stride(0) if x.dim() == 2 and x.shape[0] > 1 else max(1, x.shape[-1])
+    return x.strides[0] // x.itemsize if x.shape[0] > 1 else max(1, x.shape[-1])
+
+
+def _check(rc, fn):
+    if rc != OOC_OK:
+        raise OocError(rc, fn)
+
+
+def ooc_dgemm(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, budget, opts=None,
+              stats=None):
+    """C ABI ooc_dgemm; returns the status code (pointers may be tensors/arrays or ints)."""
+    lib = load()
+    return lib.ooc_dgemm(transA.encode(), transB.encode(), M, N, K, alpha, _ptr(A), lda, _ptr(B), ldb,
+                         beta, _ptr(C), ldc, budget, ctypes.byref(opts) if opts is not None else None,
+                         ctypes.byref(stats) if stats is not None else None)
+
+
+def ooc_sgemm(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, budget, opts=None,
+              stats=None):
+    """C ABI ooc_sgemm; returns the status code."""
+    lib = load()
+    return lib.ooc_sgemm(transA.encode(), transB.encode(), M, N, K, alpha, _ptr(A), lda, _ptr(B), ldb,
+                         beta, _ptr(C), ldc, budget, ctypes.byref(opts) if opts is not None else None,
+                         ctypes.byref(stats) if stats is not None else None)
+
+
+def ooc_dgemm_device(transA, transB, M, N, K, alpha, dA, lda, dB, ldb, beta, dC, ldc, stream=None):
+    """C ABI ooc_dgemm_device on device pointers; returns the status code."""
+    lib = load()
+    return lib.ooc_dgemm_device(transA.encode(), transB.encode(), M, N, K, alpha, _ptr(dA), lda, _ptr(dB),
+                                ldb, beta, _ptr(dC), ldc, stream)
+
+
+def ooc_plan(M, N, K, elem_bytes, beta_nonzero, budget, opts=None):
+    """C ABI ooc_plan; returns the plan as a dict (raises on error)."""
+    lib = load()
+    st = ooc_stats()
+    _check(lib.ooc_plan(M, N, K, elem_bytes, int(bool(beta_nonzero)), budget,
+                        ctypes.byref(opts) if opts is not None else None, ctypes.byref(st)), "ooc_plan")
+    return st.as_dict()
+
+
+def ooc_schedule(M, N, K, elem_bytes, beta_nonzero, budget, opts=None):
+    """C ABI ooc_schedule; returns the issued operations as a list of dicts."""
+    lib = load()
+    n = ctypes.c_int64(0)
+    o = ctypes.byref(opts) if opts is not None else None
+    rc = lib.ooc_schedule(M, N, K, elem_bytes, int(bool(beta_nonzero)), budget, o, None, 0, ctypes.byref(n))
+    if rc not in (OOC_OK, OOC_ERR_CAPACITY):
+        _check(rc, "ooc_schedule")
+    buf = (ooc_sched_op * max(1, n.value))()
+    _check(lib.ooc_schedule(M, N, K, elem_bytes, int(bool(beta_nonzero)), budget, o, buf, n.value,
+                            ctypes.byref(n)), "ooc_schedule")
+    out = []
+    for k in range(n.value):
+        e = buf[k]
+        out.append(dict(kind=e.kind, stream=e.stream, event=e.event, nreads=e.nreads,
+                        write_slot=e.write_slot, write_tag=tuple(e.write_tag),
+                        read_slot=[e.read_slot[r] for r in range(e.nreads)],
+                        read_tag=[tuple(e.read_tag[r]) for r in range(e.nreads)]))
+    return out
+
+
+def ooc_query_device():
+    """C ABI ooc_query_device: (free_bytes, h2d_gbps, d2h_gbps)."""
+    lib = load()
+    f, h, d = ctypes.c_size_t(0), ctypes.c_double(0), ctypes.c_double(0)
+    _check(lib.ooc_query_device(ctypes.byref(f), ctypes.byref(h), ctypes.byref(d)), "ooc_query_device")
+    return f.value, h.value, d.value
+
+
+def ooc_strerror(code):
+    return load().ooc_strerror(code).decode()
+
+
+def ooc_last_error():
+    return load().ooc_last_error().decode()
+
+
+# ------------------------------------------------------------------ helpers --
+def _shape_args(transA, transB, A, B, C):
+    M = A.shape[0] if transA in "Nn" else A.shape[1]
+    K = A.shape[1] if transA in "Nn" else A.shape[0]
+    N = B.shape[1] if transB in "Nn" else B.shape[0]
+    assert tuple(C.shape) == (M, N)
+    return M, N, K
+
+
+def dgemm(A, B, C, alpha=1.0, beta=0.0, budget=4 << 30, transA="N", transB="N", opts=None):
+    """In place C = alpha*op(A)*op(B) + beta*C on pinned float64 host tensors; returns stats dict."""
+    M, N, K = _shape_args(transA, transB, A, B, C)
+    st = ooc_stats()
+    _check(ooc_dgemm(transA, transB, M, N, K, alpha, A, _ld(A), B, _ld(B), beta, C, _ld(C), budget,
+                     opts, st), "ooc_dgemm")
+    return st.as_dict()
+
+
+def sgemm(A, B, C, alpha=1.0, beta=0.0, budget=4 << 30, transA="N", transB="N", opts=None):
+    """In place FP32 C = alpha*op(A)*op(B) + beta*C (BF16x3 form) on pinned float32 host tensors."""
+    M, N, K = _shape_args(transA, transB, A, B, C)
+    st = ooc_stats()
+    _check(ooc_sgemm(transA, transB, M, N, K, alpha, A, _ld(A), B, _ld(B), beta, C, _ld(C), budget,
+                     opts, st), "ooc_sgemm")
+    return st.as_dict()

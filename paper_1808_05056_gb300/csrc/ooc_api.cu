@@ -1,0 +1,588 @@
+// C ABI of libooc (declared in include/ooc.h): argument checks, the
+// out-of-core executor that issues a planned schedule on three CUDA streams
+// (H2D copy engine, compute, D2H copy engine) with events, and the in-core
+// device entry point.
+//
+// The executor follows Section IV of the libhclooc paper: the stages S(b_j),
+// S(a_i), S(c_ij), the block GEMM and R(c_ij) are asynchronous operations
+// ordered only by recorded/waited events, so copies in both directions run
+// on the copy engines while the tile kernels run.  Unlike the paper's two
+// round-robin streams, each direction and the compute have their own stream,
+// and the slot ring may be deeper than two.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "ooc_internal.hpp"
+
+namespace ooc {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+int device_sm_count()
+{
+    static int sms = -1;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        int dev = 0, n = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0)
+            sms = n;
+        else {
+            cudaGetLastError();
+            sms = 152;  // GB300 (planning without a device)
+        }
+    });
+    return sms;
+}
+
+// ------------------------------------------------------------ tensor maps --
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+int encode_map_2d(void* map_out, int dtype, const void* base, uint64_t inner, uint64_t outer, uint64_t ld_elems,
+                  uint32_t box_inner, uint32_t box_outer, int swizzle128, std::string& why)
+{
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) {
+        why = "cuTensorMapEncodeTiled unavailable";
+        return OOC_ERR_CUDA;
+    }
+    CUtensorMapDataType dt = dtype == 0   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                             : dtype == 1 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                          : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const uint64_t es = dtype == 0 ? 8 : dtype == 1 ? 2 : 4;
+    cuuint64_t dims[2] = {inner, outer};
+    cuuint64_t strides[1] = {ld_elems * es};
+    cuuint32_t box[2] = {box_inner, box_outer};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(reinterpret_cast<CUtensorMap*>(map_out), dt, 2, const_cast<void*>(base), dims, strides, box,
+                    estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        why = "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")";
+        return OOC_ERR_CUDA;
+    }
+    return OOC_OK;
+}
+
+}  // namespace ooc
+
+using namespace ooc;
+
+namespace {
+
+bool is_n(char t) { return t == 'N' || t == 'n'; }
+bool is_t(char t) { return t == 'T' || t == 't'; }
+
+int fail(int code, const std::string& msg)
+{
+    set_error(msg);
+    return code;
+}
+
+int check_device(std::string& why)
+{
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) {
+        cudaGetLastError();
+        why = "no CUDA device";
+        return OOC_ERR_NO_DEVICE;
+    }
+    int dev = 0, maj = 0, min = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&maj, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&min, cudaDevAttrComputeCapabilityMinor, dev);
+    if (maj != 10 || min != 3) {
+        why = "device is sm_" + std::to_string(maj) + std::to_string(min) + ", library is built for sm_103a";
+        return OOC_ERR_NO_DEVICE;
+    }
+    return OOC_OK;
+}
+
+int validate(char ta, char tb, int64_t M, int64_t N, int64_t K, const void* A, int64_t lda, const void* B,
+             int64_t ldb, const void* C, int64_t ldc, bool beta_nz, std::string& why)
+{
+    if (!(is_n(ta) || is_t(ta)) || !(is_n(tb) || is_t(tb))) {
+        why = "trans must be 'N' or 'T'";
+        return OOC_ERR_INVALID_ARG;
+    }
+    if (M < 0 || N < 0 || K < 0) {
+        why = "negative dimension";
+        return OOC_ERR_INVALID_ARG;
+    }
+    const int64_t a_cols = is_t(ta) ? M : K, b_cols = is_t(tb) ? K : N;
+    if (lda < std::max<int64_t>(1, a_cols) || ldb < std::max<int64_t>(1, b_cols) || ldc < std::max<int64_t>(1, N)) {
+        why = "leading dimension below the row width";
+        return OOC_ERR_INVALID_ARG;
+    }
+    if (M == 0 || N == 0) return OOC_OK;  // quick return: no operand is touched
+    if ((K > 0 && !A) || (K > 0 && !B) || !C) {
+        why = "null operand pointer";
+        return OOC_ERR_INVALID_ARG;
+    }
+    (void)beta_nz;
+    return OOC_OK;
+}
+
+bool pinned(const void* p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
+bool range_pinned(const void* base, int64_t rows, int64_t cols, int64_t ld, int es)
+{
+    if (rows <= 0 || cols <= 0) return true;
+    const char* b = static_cast<const char*>(base);
+    const char* last = b + ((rows - 1) * ld + cols - 1) * es;
+    return pinned(b) && pinned(last);
+}
+
+// OOC_FAULT_INJECT=alloc | copy:<n> | kernel:<n>  (host-side failures for tests)
+struct Inject {
+    bool alloc = false;
+    long copy = -1, kernel = -1;
+    Inject()
+    {
+        const char* e = std::getenv("OOC_FAULT_INJECT");
+        if (!e) return;
+        std::string s(e);
+        if (s == "alloc") alloc = true;
+        else if (s.rfind("copy:", 0) == 0) copy = std::atol(s.c_str() + 5);
+        else if (s.rfind("kernel:", 0) == 0) kernel = std::atol(s.c_str() + 7);
+    }
+};
+
+struct Operands {
+    const void* A;
+    int64_t lda;
+    const void* B;
+    int64_t ldb;
+    void* C;
+    int64_t ldc;
+    double alpha, beta;
+};
+
+// Resources of one call, released in the destructor after the streams drain.
+struct Exec {
+    Plan p;
+    char* arena = nullptr;
+    bool own_arena = false;
+    cudaStream_t st[3] = {nullptr, nullptr, nullptr};
+    std::vector<cudaEvent_t> ev;
+    std::vector<cudaEvent_t> kev;  // timing pairs around tile kernels
+    cudaEvent_t t_begin = nullptr, t_end[3] = {nullptr, nullptr, nullptr};
+
+    Exec() = default;
+    Exec(const Exec&) = delete;
+    Exec& operator=(const Exec&) = delete;
+    ~Exec() { release(); }
+
+    void release()
+    {
+        for (auto s : st)
+            if (s) cudaStreamSynchronize(s);
+        for (auto& e : ev) { if (e) cudaEventDestroy(e); e = nullptr; }
+        for (auto& e : kev) { if (e) cudaEventDestroy(e); e = nullptr; }
+        if (t_begin) cudaEventDestroy(t_begin);
+        t_begin = nullptr;
+        for (auto& e : t_end) { if (e) cudaEventDestroy(e); e = nullptr; }
+        for (auto& s : st) { if (s) cudaStreamDestroy(s); s = nullptr; }
+        if (own_arena && arena) cudaFree(arena);
+        arena = nullptr;
+        own_arena = false;
+        cudaGetLastError();
+    }
+};
+
+#define CK(call)                                                                           \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) return fail(OOC_ERR_CUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
+    } while (0)
+
+int launch_tile(const Plan& p, const Op& op, Exec& x, const Operands& o, std::string& why)
+{
+    const int sa = op.nr > 0 && op.rslot[0] < p.nA ? op.rslot[0] : -1;
+    int sb = -1;
+    for (int r = 0; r < op.nr; ++r)
+        if (op.rslot[r] >= p.nA && op.rslot[r] < p.nA + p.nB) sb = op.rslot[r];
+    const int sc = op.wslot;
+    const int64_t rows = p.rows_of(op.i), cols = p.cols_of(op.j), kk = p.K > 0 ? p.k_of(op.kc) : 0;
+    const double beta_eff = op.first ? o.beta : 1.0;
+    const bool read_c = !op.first || o.beta != 0.0;
+    int* err = reinterpret_cast<int*>(x.arena);
+    if (p.form == OOC_FORM_FP64) {
+        const double* dA = sa >= 0 ? reinterpret_cast<const double*>(x.arena + slot_offset(p, sa)) : nullptr;
+        const double* dB = sb >= 0 ? reinterpret_cast<const double*>(x.arena + slot_offset(p, sb)) : nullptr;
+        double* dC = reinterpret_cast<double*>(x.arena + slot_offset(p, sc));
+        return launch_fp64_tile(!p.ta, p.tb, rows, cols, kk, o.alpha, dA, p.lda_dev, dB, p.ldb_dev, beta_eff, read_c,
+                                dC, p.ldc_dev, err, x.st[kStreamCompute], why);
+    }
+    why = "contraction form not available in this build";
+    return OOC_ERR_UNSUPPORTED;
+}
+
+int run_ooc(char ta, char tb, int64_t M, int64_t N, int64_t K, const Operands& o, int es, size_t budget,
+            const ooc_opts* opts_in, ooc_stats* stats)
+{
+    const auto t_host0 = std::chrono::steady_clock::now();
+    std::string why;
+    int rc = validate(ta, tb, M, N, K, o.A, o.lda, o.B, o.ldb, o.C, o.ldc, o.beta != 0.0, why);
+    if (rc) return fail(rc, why);
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    if (M == 0 || N == 0) return OOC_OK;
+    rc = check_device(why);
+    if (rc) return fail(rc, why);
+    if (!range_pinned(o.A, is_t(ta) ? K : M, is_t(ta) ? M : K, o.lda, es) ||
+        !range_pinned(o.B, is_t(tb) ? N : K, is_t(tb) ? K : N, o.ldb, es) || !range_pinned(o.C, M, N, o.ldc, es))
+        return fail(OOC_ERR_NOT_PINNED, "host operands must be page-locked (cudaHostAlloc / cudaHostRegister)");
+
+    ooc_opts opts;
+    std::memset(&opts, 0, sizeof(opts));
+    if (opts_in) opts = *opts_in;
+    PlanRequest rq{M, N, K, es, o.beta != 0.0, is_t(ta), is_t(tb), budget, opts};
+    double hg = 0, dg = 0;
+    if (ooc_query_device(nullptr, &hg, &dg) == OOC_OK && hg > 0 && dg > 0) {
+        rq.h2d_gbps = hg;
+        rq.d2h_gbps = dg;
+    }
+    Exec x;
+    rc = make_plan(rq, x.p, why);
+    if (rc) return fail(rc, why);
+    const Plan& p = x.p;
+    std::vector<Op> ops;
+    build_schedule(p, ops);
+
+    Inject inj;
+    if (opts.workspace) {
+        if (opts.workspace_bytes < p.device_bytes)
+            return fail(OOC_ERR_INVALID_ARG, "workspace smaller than the plan's device bytes");
+        x.arena = static_cast<char*>(opts.workspace);
+    } else {
+        if (inj.alloc) return fail(OOC_ERR_INJECTED, "injected arena allocation failure");
+        if (cudaMalloc(&x.arena, p.device_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            x.arena = nullptr;
+            return fail(OOC_ERR_ALLOC, "device arena of " + std::to_string(p.device_bytes) + " bytes");
+        }
+        x.own_arena = true;
+    }
+    for (auto& s : x.st) CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    x.ev.resize(n_events(p), nullptr);
+    for (auto& e : x.ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    int64_t nkern = 0;
+    for (const Op& op : ops) nkern += op.kind == kKernel;
+    x.kev.resize(2 * nkern, nullptr);
+    for (auto& e : x.kev) CK(cudaEventCreate(&e));
+    CK(cudaEventCreate(&x.t_begin));
+    for (auto& e : x.t_end) CK(cudaEventCreate(&e));
+
+    int* err = reinterpret_cast<int*>(x.arena);
+    CK(cudaEventRecord(x.t_begin, x.st[kStreamH2D]));
+    CK(cudaStreamWaitEvent(x.st[kStreamCompute], x.t_begin, 0));
+    CK(cudaStreamWaitEvent(x.st[kStreamD2H], x.t_begin, 0));
+    CK(cudaMemsetAsync(err, 0, sizeof(int), x.st[kStreamCompute]));
+
+    long n_copy = 0, n_kern = 0;
+    double h2d = 0, d2h = 0;
+    const char* hA = static_cast<const char*>(o.A);
+    const char* hB = static_cast<const char*>(o.B);
+    char* hC = static_cast<char*>(o.C);
+    for (const Op& op : ops) {
+        cudaStream_t s = x.st[op.stream];
+        switch (op.kind) {
+        case kRecord: CK(cudaEventRecord(x.ev[op.event], s)); break;
+        case kWait: CK(cudaStreamWaitEvent(s, x.ev[op.event], 0)); break;
+        case kH2D: {
+            if (inj.copy >= 0 && n_copy++ == inj.copy) return fail(OOC_ERR_INJECTED, "injected copy failure");
+            const Tag& t = op.wtag;
+            char* dst = x.arena + slot_offset(p, op.wslot);
+            const char* src;
+            int64_t rows, width, spitch, dpitch;
+            if (t.m == kMatA) {
+                const int64_t r0 = t.r * p.mb, k0 = t.c * p.kb, mr = p.rows_of(t.r), kr = p.k_of(t.c);
+                if (!p.ta) { src = hA + (r0 * o.lda + k0) * es; rows = mr; width = kr; }
+                else { src = hA + (k0 * o.lda + r0) * es; rows = kr; width = mr; }
+                spitch = o.lda * es; dpitch = p.lda_dev * es;
+            } else if (t.m == kMatB) {
+                const int64_t k0 = t.r * p.kb, c0 = t.c * p.nb, kr = p.k_of(t.r), nc = p.cols_of(t.c);
+                if (!p.tb) { src = hB + (k0 * o.ldb + c0) * es; rows = kr; width = nc; }
+                else { src = hB + (c0 * o.ldb + k0) * es; rows = nc; width = kr; }
+                spitch = o.ldb * es; dpitch = p.ldb_dev * es;
+            } else {
+                src = hC + (t.r * p.mb * o.ldc + t.c * p.nb) * es;
+                rows = p.rows_of(t.r); width = p.cols_of(t.c);
+                spitch = o.ldc * es; dpitch = p.ldc_dev * es;
+            }
+            if (rows > 0 && width > 0) {
+                CK(cudaMemcpy2DAsync(dst, dpitch, src, spitch, width * es, rows, cudaMemcpyHostToDevice, s));
+                h2d += (double)rows * width * es;
+            }
+            break;
+        }
+        case kKernel: {
+            if (inj.kernel >= 0 && n_kern == inj.kernel) return fail(OOC_ERR_INJECTED, "injected kernel failure");
+            CK(cudaEventRecord(x.kev[2 * n_kern], s));
+            rc = launch_tile(p, op, x, o, why);
+            if (rc) return fail(rc, why);
+            CK(cudaEventRecord(x.kev[2 * n_kern + 1], s));
+            ++n_kern;
+            break;
+        }
+        case kD2H: {
+            const int64_t rows = p.rows_of(op.i), width = p.cols_of(op.j);
+            char* dst = hC + (op.i * p.mb * o.ldc + op.j * p.nb) * es;
+            const char* src = x.arena + slot_offset(p, op.rslot[0]);
+            CK(cudaMemcpy2DAsync(dst, o.ldc * es, src, p.ldc_dev * es, width * es, rows, cudaMemcpyDeviceToHost, s));
+            d2h += (double)rows * width * es;
+            break;
+        }
+        }
+    }
+    for (int i = 0; i < 3; ++i) CK(cudaEventRecord(x.t_end[i], x.st[i]));
+    for (auto s : x.st) CK(cudaStreamSynchronize(s));
+    int herr = 0;
+    CK(cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (herr != 0) return fail(OOC_ERR_TIMEOUT, "a device-side wait gave up (status " + std::to_string(herr) + ")");
+
+    if (stats) {
+        float ms = 0, best = 0;
+        for (auto e : x.t_end) {
+            CK(cudaEventElapsedTime(&ms, x.t_begin, e));
+            best = std::max(best, ms);
+        }
+        double ksum = 0;
+        for (int64_t k = 0; k < n_kern; ++k) {
+            CK(cudaEventElapsedTime(&ms, x.kev[2 * k], x.kev[2 * k + 1]));
+            ksum += ms;
+        }
+        stats->device_seconds = best * 1e-3;
+        stats->kernel_seconds = ksum * 1e-3;
+        stats->h2d_bytes = h2d;
+        stats->d2h_bytes = d2h;
+        stats->mb = p.mb; stats->nb = p.nb; stats->kb = p.kb;
+        stats->depth = p.nA; stats->c_buffers = p.nC; stats->b_buffers = p.nB; stats->form = p.form;
+        stats->blocks = p.h * p.w; stats->steps = p.h * p.w * p.nkc;
+        stats->device_bytes = (int64_t)p.device_bytes;
+        stats->slices = p.slices; stats->products = p.products;
+    }
+    // release before taking the wall time (the arena free is part of the call)
+    x.release();
+    if (stats) {
+        stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_host0).count();
+        stats->tflops = stats->seconds > 0 ? 2.0 * (double)M * N * K / stats->seconds / 1e12 : 0.0;
+    }
+    return OOC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ooc_strerror(int code)
+{
+    switch (code) {
+    case OOC_OK: return "ok";
+    case OOC_ERR_INVALID_ARG: return "invalid argument";
+    case OOC_ERR_BUDGET: return "device budget too small for any plan";
+    case OOC_ERR_NOT_PINNED: return "host operand not page-locked";
+    case OOC_ERR_CUDA: return "CUDA call failed";
+    case OOC_ERR_NO_DEVICE: return "no usable sm_103 device";
+    case OOC_ERR_TIMEOUT: return "device-side wait timed out";
+    case OOC_ERR_ALLOC: return "device allocation failed";
+    case OOC_ERR_UNSUPPORTED: return "unsupported form or option";
+    case OOC_ERR_INJECTED: return "injected failure";
+    case OOC_ERR_CAPACITY: return "output array too small";
+    default: return "unknown status";
+    }
+}
+
+const char* ooc_last_error(void) { return g_last_error.c_str(); }
+
+int ooc_plan(int64_t M, int64_t N, int64_t K, int32_t elem_bytes, int32_t beta_nonzero, size_t budget,
+             const ooc_opts* opts_in, ooc_stats* out)
+{
+    if ((elem_bytes != 4 && elem_bytes != 8) || M <= 0 || N <= 0 || K < 0 || !out)
+        return fail(OOC_ERR_INVALID_ARG, "ooc_plan: bad arguments");
+    ooc_opts opts;
+    std::memset(&opts, 0, sizeof(opts));
+    if (opts_in) opts = *opts_in;
+    PlanRequest rq{M, N, K, elem_bytes, beta_nonzero != 0, false, false, budget, opts};
+    Plan p;
+    std::string why;
+    int rc = make_plan(rq, p, why);
+    if (rc) return fail(rc, why);
+    std::memset(out, 0, sizeof(*out));
+    out->mb = p.mb; out->nb = p.nb; out->kb = p.kb;
+    out->depth = p.nA; out->c_buffers = p.nC; out->b_buffers = p.nB; out->form = p.form;
+    out->blocks = p.h * p.w; out->steps = p.h * p.w * p.nkc;
+    out->device_bytes = (int64_t)p.device_bytes;
+    out->h2d_bytes = p.h2d_bytes; out->d2h_bytes = p.d2h_bytes;
+    out->slices = p.slices; out->products = p.products;
+    out->seconds = p.est_seconds;
+    return OOC_OK;
+}
+
+int ooc_schedule(int64_t M, int64_t N, int64_t K, int32_t elem_bytes, int32_t beta_nonzero, size_t budget,
+                 const ooc_opts* opts_in, ooc_sched_op* out, int64_t capacity, int64_t* count)
+{
+    if ((elem_bytes != 4 && elem_bytes != 8) || M <= 0 || N <= 0 || K < 0 || !count)
+        return fail(OOC_ERR_INVALID_ARG, "ooc_schedule: bad arguments");
+    ooc_opts opts;
+    std::memset(&opts, 0, sizeof(opts));
+    if (opts_in) opts = *opts_in;
+    PlanRequest rq{M, N, K, elem_bytes, beta_nonzero != 0, false, false, budget, opts};
+    Plan p;
+    std::string why;
+    int rc = make_plan(rq, p, why);
+    if (rc) return fail(rc, why);
+    std::vector<Op> ops;
+    build_schedule(p, ops);
+    *count = (int64_t)ops.size();
+    if (!out || capacity < (int64_t)ops.size()) return fail(OOC_ERR_CAPACITY, "schedule needs more entries");
+    for (size_t n = 0; n < ops.size(); ++n) {
+        const Op& o = ops[n];
+        ooc_sched_op& d = out[n];
+        d.kind = o.kind; d.stream = o.stream; d.event = o.event; d.nreads = o.nr;
+        d.write_slot = o.wslot;
+        const int64_t wt[4] = {o.wtag.m, o.wtag.r, o.wtag.c, o.wtag.v};
+        std::memcpy(d.write_tag, wt, sizeof(wt));
+        for (int r = 0; r < 3; ++r) {
+            d.read_slot[r] = o.rslot[r];
+            const int64_t rt[4] = {o.rtag[r].m, o.rtag[r].r, o.rtag[r].c, o.rtag[r].v};
+            std::memcpy(d.read_tag[r], rt, sizeof(rt));
+        }
+    }
+    return OOC_OK;
+}
+
+int ooc_query_device(size_t* free_bytes, double* h2d_gbps, double* d2h_gbps)
+{
+    std::string why;
+    int rc = check_device(why);
+    if (rc) return fail(rc, why);
+    if (free_bytes) {
+        size_t f = 0, t = 0;
+        if (cudaMemGetInfo(&f, &t) != cudaSuccess) return fail(OOC_ERR_CUDA, "cudaMemGetInfo");
+        *free_bytes = f;
+    }
+    if (!h2d_gbps && !d2h_gbps) return OOC_OK;
+    static double hg = 0, dg = 0;
+    static int qrc = OOC_OK;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        const size_t bytes = 256ull << 20;
+        void *h = nullptr, *d = nullptr;
+        cudaStream_t s = nullptr;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (cudaHostAlloc(&h, bytes, cudaHostAllocDefault) != cudaSuccess || cudaMalloc(&d, bytes) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+            cudaEventCreate(&e1) != cudaSuccess) {
+            qrc = OOC_ERR_CUDA;
+        } else {
+            std::memset(h, 0, bytes);
+            for (int dir = 0; dir < 2; ++dir) {
+                float best = 1e30f;
+                for (int r = 0; r < 4; ++r) {
+                    cudaEventRecord(e0, s);
+                    if (dir == 0) cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, s);
+                    else cudaMemcpyAsync(h, d, bytes, cudaMemcpyDeviceToHost, s);
+                    cudaEventRecord(e1, s);
+                    cudaEventSynchronize(e1);
+                    float ms = 0;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (r > 0) best = std::min(best, ms);
+                }
+                (dir == 0 ? hg : dg) = (double)bytes / (best * 1e-3) / 1e9;
+            }
+        }
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (s) cudaStreamDestroy(s);
+        if (d) cudaFree(d);
+        if (h) cudaFreeHost(h);
+        cudaGetLastError();
+    });
+    if (qrc) return fail(qrc, "link bandwidth probe failed");
+    if (h2d_gbps) *h2d_gbps = hg;
+    if (d2h_gbps) *d2h_gbps = dg;
+    return OOC_OK;
+}
+
+int ooc_dgemm(char transA, char transB, int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t lda,
+              const double* B, int64_t ldb, double beta, double* C, int64_t ldc, size_t device_budget_bytes,
+              const ooc_opts* opts, ooc_stats* stats)
+{
+    Operands o{A, lda, B, ldb, C, ldc, alpha, beta};
+    return run_ooc(transA, transB, M, N, K, o, 8, device_budget_bytes, opts, stats);
+}
+
+int ooc_sgemm(char transA, char transB, int64_t M, int64_t N, int64_t K, float alpha, const float* A, int64_t lda,
+              const float* B, int64_t ldb, float beta, float* C, int64_t ldc, size_t device_budget_bytes,
+              const ooc_opts* opts, ooc_stats* stats)
+{
+    Operands o{A, lda, B, ldb, C, ldc, (double)alpha, (double)beta};
+    return run_ooc(transA, transB, M, N, K, o, 4, device_budget_bytes, opts, stats);
+}
+
+int ooc_dgemm_device(char transA, char transB, int64_t M, int64_t N, int64_t K, double alpha, const double* dA,
+                     int64_t lda, const double* dB, int64_t ldb, double beta, double* dC, int64_t ldc, void* stream)
+{
+    std::string why;
+    int rc = validate(transA, transB, M, N, K, dA, lda, dB, ldb, dC, ldc, beta != 0.0, why);
+    if (rc) return fail(rc, why);
+    if (M == 0 || N == 0) return OOC_OK;
+    rc = check_device(why);
+    if (rc) return fail(rc, why);
+    // TMA needs 16-byte aligned bases and row pitches; the epilogue stores pairs
+    if ((lda % 2) || (ldb % 2) || (ldc % 2) || (reinterpret_cast<uintptr_t>(dA) % 16) ||
+        (reinterpret_cast<uintptr_t>(dB) % 16) || (reinterpret_cast<uintptr_t>(dC) % 16))
+        return fail(OOC_ERR_UNSUPPORTED, "device operands need 16-byte aligned bases and even leading dimensions");
+    static int* err = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        if (cudaMalloc(&err, sizeof(int)) == cudaSuccess) cudaMemset(err, 0, sizeof(int));
+        else err = nullptr;
+    });
+    if (!err) return fail(OOC_ERR_ALLOC, "error word");
+    rc = launch_fp64_tile(is_n(transA), is_t(transB), M, N, K, alpha, dA, lda, dB, ldb, beta, beta != 0.0, dC, ldc,
+                          err, stream, why);
+    if (rc) return fail(rc, why);
+    return OOC_OK;
+}
+
+}  // extern "C"

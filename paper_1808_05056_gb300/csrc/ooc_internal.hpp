@@ -1,0 +1,110 @@
+// Internal interfaces of libooc: the plan, the issued schedule and the kernel
+// launchers.  Host-only declarations; nothing here is exported.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/ooc.h"
+
+namespace ooc {
+
+// ---------------------------------------------------------------- plan ----
+// One out-of-core plan: C is cut into h x w blocks of mb x nb, K into nkc
+// chunks of kb (Section IV partitioner, generalised with K-chunks and
+// ragged edges); A chunks (mb x kb), B chunks (kb x nb) and C blocks live in
+// rings of device slots.
+struct Plan {
+    int64_t M = 0, N = 0, K = 0;
+    int32_t es = 8;          // host element bytes (8 FP64, 4 FP32)
+    int32_t form = OOC_FORM_FP64;
+    bool beta_nz = false;
+    bool ta = false, tb = false;
+    bool paper = false;
+    int64_t mb = 0, nb = 0, kb = 0;
+    int64_t h = 0, w = 0, nkc = 0;
+    int32_t nA = 0, nB = 0, nC = 0;
+    int32_t slices = 0, products = 0;
+    // device layout (bytes); each slot is 256-byte aligned
+    size_t a_slot = 0, b_slot = 0, c_slot = 0;      // raw operand slots
+    size_t a_aux = 0, b_aux = 0, c_aux = 0;         // per-slot form scratch (split planes, FP64 acc)
+    size_t header = 256;                            // error word etc.
+    size_t device_bytes = 0;
+    double h2d_bytes = 0, d2h_bytes = 0;
+    double est_seconds = 0;
+    // device leading dimensions (elements) of the slots, per stored layout
+    int64_t lda_dev = 0, ldb_dev = 0, ldc_dev = 0;
+
+    int64_t rows_of(int64_t i) const { return (i + 1) * mb <= M ? mb : M - i * mb; }
+    int64_t cols_of(int64_t j) const { return (j + 1) * nb <= N ? nb : N - j * nb; }
+    int64_t k_of(int64_t c) const { return (c + 1) * kb <= K ? kb : K - c * kb; }
+    int32_t slots() const { return nA + nB + nC; }
+};
+
+struct PlanRequest {
+    int64_t M, N, K;
+    int32_t es;
+    bool beta_nz, ta, tb;
+    size_t budget;
+    ooc_opts opts;
+    double h2d_gbps = 200.0, d2h_gbps = 190.0;  // link model for the estimate
+};
+
+// Returns OOC_OK and fills `plan`, or an error code with a message in `why`.
+int make_plan(const PlanRequest& rq, Plan& plan, std::string& why);
+
+// -------------------------------------------------------------- schedule --
+enum OpKind { kH2D = 0, kKernel = 1, kD2H = 2, kRecord = 3, kWait = 4 };
+enum StreamId { kStreamH2D = 0, kStreamCompute = 1, kStreamD2H = 2 };
+enum MatId { kMatA = 0, kMatB = 1, kMatC = 2 };
+
+struct Tag {
+    int64_t m = -1, r = -1, c = -1, v = -1;
+    bool operator==(const Tag& o) const { return m == o.m && r == o.r && c == o.c && v == o.v; }
+};
+
+struct Op {
+    int32_t kind = 0, stream = 0, event = -1;
+    int32_t wslot = -1;
+    Tag wtag;
+    int32_t nr = 0;
+    int32_t rslot[3] = {-1, -1, -1};
+    Tag rtag[3];
+    // execution detail
+    int64_t i = 0, j = 0, kc = 0;  // block row, block column, K chunk
+    bool first = false, last = false;
+};
+
+// Events: ready(s) after a load into slot s, free(s) after a kernel read s,
+// out(s) after the D2H of C slot s, done(s) after the last kernel of C slot s.
+inline int32_t ev_ready(const Plan& p, int32_t s) { return s; }
+inline int32_t ev_free(const Plan& p, int32_t s) { return p.slots() + s; }
+inline int32_t ev_out(const Plan& p, int32_t s) { return 2 * p.slots() + s; }
+inline int32_t ev_done(const Plan& p, int32_t s) { return 3 * p.slots() + s; }
+inline int32_t n_events(const Plan& p) { return 4 * p.slots(); }
+
+void build_schedule(const Plan& plan, std::vector<Op>& ops);
+
+// slot byte offsets inside the arena
+size_t slot_offset(const Plan& p, int32_t slot);
+size_t slot_aux_offset(const Plan& p, int32_t slot);
+
+// ---------------------------------------------------------- kernel side --
+// Tensor-map encoder (driver entry point fetched at first use).
+int encode_map_2d(void* map_out, int dtype /*0 f64, 1 bf16, 2 f32*/, const void* base,
+                  uint64_t inner, uint64_t outer, uint64_t ld_elems, uint32_t box_inner,
+                  uint32_t box_outer, int swizzle128, std::string& why);
+
+// FP64 tile GEMM on device operands (one C block, one K chunk):
+// C = alpha*op(A)*op(B) + (read_c ? beta*C : 0).
+// a_kmajor: A stored rows x K (else K x rows); b_kmajor: B stored cols x K (else K x cols).
+int launch_fp64_tile(bool a_kmajor, bool b_kmajor, int64_t M, int64_t N, int64_t K, double alpha,
+                     const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
+                     bool read_c, double* C, int64_t ldc, int* err, void* stream,
+                     std::string& why);
+
+int device_sm_count();
+void set_error(const std::string& msg);
+
+}  // namespace ooc

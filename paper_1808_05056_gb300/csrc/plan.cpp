@@ -1,0 +1,473 @@
+// Host planner and schedule generator of the out-of-core GEMM.
+//
+// Planner (Section IV, partitioner paragraph): A is cut into horizontal
+// slices, B into vertical slices and C into blocks so that the buffers of the
+// pipeline fit the device budget.  Two modes:
+//   * paper mode reproduces the Section IV partitioner: h | M, w | N equal
+//     slices, whole-K slices, buffers for two A slices, one B slice and two C
+//     blocks ("any two blocks of C in the same column"), fewest blocks first,
+//     then the smaller footprint, then the larger h (the worked example's
+//     4 x 2 split of Fig. 2);
+//   * auto mode searches block rows/columns, an optional K chunk and the
+//     buffer counts, scoring each candidate with a time estimate built from
+//     the device's compute rate, tile-wave quantisation and the measured host
+//     link, and keeps the fastest that fits.
+//
+// Schedule (Section IV, five pipeline stages and the event rule that device
+// data is not overwritten until the kernels using it have completed): steps
+// run column-major over C blocks (j outer, i inner, the B slice of a column
+// stays resident as in Fig. 1's loop order), K chunks innermost.  Every load
+// picks its slot by farthest next use (ties: least recently used), waits on
+// the event recorded after the slot's last reader, and records a ready event
+// that the compute stream waits on.  H2D, compute and D2H each have a stream.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <limits>
+#include <string>
+#include <vector>
+
+#include "ooc_internal.hpp"
+
+namespace ooc {
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+struct FormModel {
+    int64_t tile_m, tile_n;  // CTA tile of the contraction kernel
+    double rate;             // sustained tile throughput, logical FLOP/s of the whole device
+    int ctas_per_sm;
+    int products;            // slice products per logical product
+    int slices;
+    double aux_a, aux_b;     // extra device bytes per element of an A / B slot (split planes)
+    double aux_c;            // extra device bytes per C element (FP64 accumulator etc.)
+};
+
+FormModel form_model(int form, int es, int64_t K, int slices_opt)
+{
+    FormModel f{};
+    if (form == OOC_FORM_FP64) {
+        f.tile_m = 64; f.tile_n = 64; f.rate = 1.0e12; f.ctas_per_sm = 3;
+        f.products = 1; f.slices = 1;
+    } else if (form == OOC_FORM_BF16X3) {
+        f.tile_m = 128; f.tile_n = 128; f.ctas_per_sm = 1;
+        f.products = 6; f.slices = 3;
+        f.rate = 1.5e15 / 6.0;
+        f.aux_a = 3 * 2; f.aux_b = 3 * 2; f.aux_c = 8;
+    } else {  // Ozaki
+        int s = slices_opt > 0 ? slices_opt : 8;
+        f.tile_m = 128; f.tile_n = 128; f.ctas_per_sm = 1;
+        f.slices = s; f.products = s * (s + 1) / 2;
+        f.rate = 1.5e15 / f.products;
+        f.aux_a = 2.0 * s + 0.0; f.aux_b = 2.0 * s; f.aux_c = 0;
+    }
+    (void)es; (void)K;
+    return f;
+}
+
+void layout(Plan& p, const FormModel& f)
+{
+    const int64_t ald = 16;  // 16 elements: 128-byte rows for FP64, 64 for FP32
+    const int64_t a_rows = p.ta ? p.kb : p.mb, a_cols = p.ta ? p.mb : p.kb;
+    const int64_t b_rows = p.tb ? p.nb : p.kb, b_cols = p.tb ? p.kb : p.nb;
+    p.lda_dev = round_up(std::max<int64_t>(a_cols, 1), ald);
+    p.ldb_dev = round_up(std::max<int64_t>(b_cols, 1), ald);
+    p.ldc_dev = round_up(std::max<int64_t>(p.nb, 1), ald);
+    p.a_slot = align_up((size_t)std::max<int64_t>(a_rows, 1) * p.lda_dev * p.es, kAlign);
+    p.b_slot = align_up((size_t)std::max<int64_t>(b_rows, 1) * p.ldb_dev * p.es, kAlign);
+    const int es_c = p.es;  // C slot holds the host element type
+    p.c_slot = align_up((size_t)p.mb * p.ldc_dev * es_c, kAlign);
+    p.a_aux = align_up((size_t)std::ceil(f.aux_a * (double)p.mb * (double)round_up(p.kb, 64)), kAlign);
+    p.b_aux = align_up((size_t)std::ceil(f.aux_b * (double)p.nb * (double)round_up(p.kb, 64)), kAlign);
+    p.c_aux = (p.nkc > 1 || p.es == 4) ? align_up((size_t)std::ceil(f.aux_c * (double)p.mb * (double)p.nb), kAlign) : 0;
+    if (p.form == OOC_FORM_OZAKI) {
+        // per-row / per-column exponents of the slot (int32 each)
+        p.a_aux += align_up((size_t)p.mb * 4, kAlign);
+        p.b_aux += align_up((size_t)p.nb * 4, kAlign);
+    }
+    p.device_bytes = p.header + (size_t)p.nA * (p.a_slot + p.a_aux) +
+                     (size_t)p.nB * (p.b_slot + p.b_aux) + (size_t)p.nC * (p.c_slot + p.c_aux);
+}
+
+// Closed-form traffic of the schedule for this plan.
+void traffic(Plan& p)
+{
+    const double es = p.es;
+    const double A = (double)p.M * p.K * es, B = (double)p.K * p.N * es, C = (double)p.M * p.N * es;
+    // A chunks are re-sent for every block column unless one column's worth stays resident
+    double a_loads = (p.h == 1 && p.nkc <= p.nA) ? A : A * p.w;
+    double b_loads = (p.nkc <= p.nB) ? B : B * p.h;
+    if (p.K == 0) a_loads = b_loads = 0;
+    p.h2d_bytes = a_loads + b_loads + (p.beta_nz ? C : 0.0);
+    p.d2h_bytes = C;
+}
+
+double estimate(const Plan& p, const FormModel& f, int sms, double h2d_gbps, double d2h_gbps)
+{
+    const double slots_total = (double)sms * f.ctas_per_sm;
+    // compute: per step waves x per-tile time, summed over full / ragged blocks
+    double t_comp = 0;
+    const int64_t hf = p.M / p.mb, wf = p.N / p.nb;
+    const int64_t mr = p.M - hf * p.mb, nr = p.N - wf * p.nb;
+    struct Part { int64_t rows, cols, count; };
+    Part parts[4] = {{p.mb, p.nb, hf * wf}, {mr, p.nb, (mr ? 1 : 0) * wf},
+                     {p.mb, nr, hf * (nr ? 1 : 0)}, {mr, nr, (mr && nr) ? 1 : 0}};
+    const double tile_time_per_k = 2.0 * f.tile_m * f.tile_n * slots_total / f.rate;
+    for (auto& pt : parts) {
+        if (pt.count == 0 || pt.rows == 0 || pt.cols == 0) continue;
+        const double tiles = (double)cdiv(pt.rows, f.tile_m) * cdiv(pt.cols, f.tile_n);
+        const double waves = std::ceil(tiles / slots_total);
+        t_comp += pt.count * waves * tile_time_per_k * (double)p.K;
+    }
+    const double bw_h = h2d_gbps * 1e9, bw_d = d2h_gbps * 1e9;
+    const double t_link = std::max({p.h2d_bytes / bw_h, p.d2h_bytes / bw_d,
+                                    (p.h2d_bytes + p.d2h_bytes) / (0.85 * (bw_h + bw_d))});
+    const double es = p.es;
+    const double fill = ((double)p.mb * p.kb + (double)p.kb * p.nb * std::min<int64_t>(p.nkc, p.nB)) * es / bw_h;
+    const double drain = (double)p.mb * p.nb * es / bw_d;
+    double bubbles = 0;
+    if (p.nB < 2 * p.nkc && p.nkc <= p.nB) bubbles = (double)(p.w - 1) * p.K * p.nb * es / bw_h;
+    const double steps = (double)p.h * p.w * p.nkc;
+    return std::max(t_comp, t_link) + fill + drain + bubbles + steps * 8e-6;
+}
+
+bool paper_plan(const PlanRequest& rq, Plan& best, std::string& why)
+{
+    const int64_t M = rq.M, N = rq.N, K = rq.K;
+    const double mem = (double)rq.budget / rq.es;  // elements, as Section IV counts them
+    bool found = false;
+    int64_t bh = 0, bw = 0;
+    double bkey0 = 0, bkey1 = 0;
+    for (int64_t h = 1; h <= M; ++h) {
+        if (M % h) continue;
+        for (int64_t w = 1; w <= N; ++w) {
+            if (N % w) continue;
+            const double mb = (double)(M / h), nb = (double)(N / w);
+            const double fp = 2 * mb * K + K * nb + 2 * mb * nb;
+            if (fp > mem) continue;
+            const double k0 = (double)h * w, k1 = fp;
+            bool better = !found || k0 < bkey0 || (k0 == bkey0 && (k1 < bkey1 || (k1 == bkey1 && h > bh)));
+            if (better) { found = true; bh = h; bw = w; bkey0 = k0; bkey1 = k1; }
+        }
+    }
+    if (!found) {
+        why = "no equal h x w split fits 2A + 1B + 2C in the budget";
+        return false;
+    }
+    best.mb = M / bh; best.nb = N / bw; best.kb = std::max<int64_t>(K, 1);
+    best.nA = 2; best.nB = 1; best.nC = 2;
+    return true;
+}
+
+}  // namespace
+
+int make_plan(const PlanRequest& rq, Plan& p, std::string& why)
+{
+    p = Plan{};
+    p.M = rq.M; p.N = rq.N; p.K = rq.K; p.es = rq.es;
+    p.beta_nz = rq.beta_nz; p.ta = rq.ta; p.tb = rq.tb;
+    int form = rq.opts.form;
+    if (form == OOC_FORM_AUTO) form = (rq.es == 8) ? OOC_FORM_FP64 : OOC_FORM_BF16X3;
+    if (rq.es == 8 && form != OOC_FORM_FP64 && form != OOC_FORM_OZAKI) {
+        why = "ooc_dgemm supports the FP64 and Ozaki forms";
+        return OOC_ERR_INVALID_ARG;
+    }
+    if (rq.es == 4 && form != OOC_FORM_BF16X3) {
+        why = "ooc_sgemm supports the BF16x3 form";
+        return OOC_ERR_INVALID_ARG;
+    }
+    p.form = form;
+    const FormModel f = form_model(form, rq.es, rq.K, rq.opts.slices);
+    p.slices = f.slices; p.products = f.products;
+    const int sms = device_sm_count();
+    if (rq.M <= 0 || rq.N <= 0) {
+        why = "empty problem";
+        return OOC_ERR_INVALID_ARG;
+    }
+
+    if (rq.opts.flags & OOC_PLAN_PAPER) {
+        if (!paper_plan(rq, p, why)) return OOC_ERR_BUDGET;
+        p.paper = true;
+        p.h = rq.M / p.mb; p.w = rq.N / p.nb; p.nkc = 1;
+        layout(p, f);
+        traffic(p);
+        p.est_seconds = estimate(p, f, sms, rq.h2d_gbps, rq.d2h_gbps);
+        return OOC_OK;
+    }
+
+    // candidate block sizes: equal splits rounded up to the kernel tile
+    auto sizes = [](int64_t X, int64_t g, int64_t forced) {
+        std::vector<int64_t> v;
+        if (forced > 0) { v.push_back(std::min(forced, X)); return v; }
+        for (int64_t parts = 1; parts <= 4096; parts = parts < 16 ? parts + 1 : parts * 5 / 4) {
+            int64_t s = round_up(cdiv(X, parts), g);
+            if (s > X) s = X;
+            if (s < 1) continue;
+            if (std::find(v.begin(), v.end(), s) == v.end()) v.push_back(s);
+            if (s <= g) break;
+        }
+        // below one kernel tile, for very small budgets
+        for (int64_t s = g / 2; s >= 8; s /= 2)
+            if (s < X && std::find(v.begin(), v.end(), s) == v.end()) v.push_back(s);
+        return v;
+    };
+    const std::vector<int64_t> mbs = sizes(rq.M, f.tile_m, rq.opts.mb);
+    const std::vector<int64_t> nbs = sizes(rq.N, f.tile_n, rq.opts.nb);
+    std::vector<int64_t> kbs;
+    if (rq.opts.kb > 0) kbs.push_back(std::min<int64_t>(rq.opts.kb, std::max<int64_t>(rq.K, 1)));
+    else {
+        kbs.push_back(std::max<int64_t>(rq.K, 1));
+        for (int64_t c = 2; c <= 1024 && rq.K > 64; c = c < 8 ? c + 1 : c * 2) {
+            int64_t kb = round_up(cdiv(rq.K, c), 64);
+            if (kb >= rq.K) continue;
+            if (std::find(kbs.begin(), kbs.end(), kb) == kbs.end()) kbs.push_back(kb);
+            if (kb <= 64) break;
+        }
+        for (int64_t kb = 32; kb >= 16; kb /= 2)
+            if (kb < rq.K) kbs.push_back(kb);
+    }
+    const std::vector<int> nAs = rq.opts.depth > 0 ? std::vector<int>{rq.opts.depth} : std::vector<int>{2, 3};
+    const std::vector<int> nCs = rq.opts.c_buffers > 0 ? std::vector<int>{rq.opts.c_buffers} : std::vector<int>{2, 3};
+
+    bool found = false;
+    Plan best;
+    double best_t = std::numeric_limits<double>::infinity();
+    for (int64_t kb : kbs) {
+        const int64_t nkc = rq.K == 0 ? 1 : cdiv(rq.K, kb);
+        std::vector<int> nBs = {(int)std::min<int64_t>(2 * nkc, 1 << 20), (int)nkc};
+        if (nkc > 2) nBs.push_back(2);
+        for (int64_t mb : mbs)
+            for (int64_t nb : nbs)
+                for (int nA : nAs)
+                    for (int nC : nCs)
+                        for (int nB : nBs) {
+                            Plan c = p;
+                            c.mb = mb; c.nb = nb; c.kb = kb;
+                            c.h = cdiv(rq.M, mb); c.w = cdiv(rq.N, nb); c.nkc = nkc;
+                            c.nA = nA; c.nB = nB; c.nC = nC;
+                            layout(c, f);
+                            if (c.device_bytes > rq.budget) continue;
+                            traffic(c);
+                            c.est_seconds = estimate(c, f, sms, rq.h2d_gbps, rq.d2h_gbps);
+                            // prefer faster; near-ties go to fewer device bytes
+                            if (!found || c.est_seconds < best_t * (1 - 1e-9) ||
+                                (c.est_seconds <= best_t * (1 + 1e-9) && c.device_bytes < best.device_bytes)) {
+                                best = c; best_t = c.est_seconds; found = true;
+                            }
+                        }
+    }
+    if (!found) {
+        why = "budget of " + std::to_string(rq.budget) + " bytes is below the smallest plan";
+        return OOC_ERR_BUDGET;
+    }
+    p = best;
+    return OOC_OK;
+}
+
+size_t slot_offset(const Plan& p, int32_t s)
+{
+    size_t off = p.header;
+    if (s < p.nA) return off + (size_t)s * (p.a_slot + p.a_aux);
+    off += (size_t)p.nA * (p.a_slot + p.a_aux);
+    s -= p.nA;
+    if (s < p.nB) return off + (size_t)s * (p.b_slot + p.b_aux);
+    off += (size_t)p.nB * (p.b_slot + p.b_aux);
+    s -= p.nB;
+    return off + (size_t)s * (p.c_slot + p.c_aux);
+}
+
+size_t slot_aux_offset(const Plan& p, int32_t s)
+{
+    const size_t base = slot_offset(p, s);
+    if (s < p.nA) return base + p.a_slot;
+    if (s < p.nA + p.nB) return base + p.b_slot;
+    return base + p.c_slot;
+}
+
+// ------------------------------------------------------------- schedule --
+namespace {
+
+struct Gen {
+    const Plan& p;
+    std::vector<Op>& ops;
+    std::vector<Tag> content;
+    std::vector<int64_t> last_use;
+    std::vector<bool> read_since_load, compute_synced, d2h_pending;
+
+    Gen(const Plan& plan, std::vector<Op>& o) : p(plan), ops(o)
+    {
+        const int S = p.slots();
+        content.assign(S, Tag{});
+        last_use.assign(S, -1);
+        read_since_load.assign(S, false);
+        compute_synced.assign(S, true);
+        d2h_pending.assign(S, false);
+        rec.assign(n_events(p), {0, 0});
+    }
+
+    int64_t step_index(int64_t i, int64_t j, int64_t kc) const { return (j * p.h + i) * p.nkc + kc; }
+
+    // next step (> t) that needs tile `tg`, or INT64_MAX
+    int64_t next_use(const Tag& tg, int64_t t) const
+    {
+        const int64_t INF = std::numeric_limits<int64_t>::max();
+        if (tg.m == kMatA) {  // (i, kc) used in every column
+            for (int64_t j = 0; j < p.w; ++j) {
+                int64_t s = step_index(tg.r, j, tg.c);
+                if (s > t) return s;
+            }
+            return INF;
+        }
+        if (tg.m == kMatB) {  // (kc, j) used by every row of column j
+            const int64_t j = tg.c, kc = tg.r;
+            const int64_t first = step_index(0, j, kc), last = step_index(p.h - 1, j, kc);
+            if (t < first) return first;
+            if (t >= last) return INF;
+            // the current row's step if this chunk comes later in it, else the next row's
+            const int64_t i_cur = (t / p.nkc) - j * p.h;
+            return step_index(i_cur, j, kc) > t ? step_index(i_cur, j, kc) : step_index(i_cur + 1, j, kc);
+        }
+        return INF;
+    }
+
+    // Stream-order bookkeeping: pos[s] counts copies/kernels issued on stream s;
+    // rec[e] is (stream, position) of event e's latest record; synced[a][b]
+    // is the last position of stream b that stream a is already ordered
+    // after.  A wait that adds no ordering is not issued.
+    int64_t pos[3] = {0, 0, 0};
+    std::vector<std::pair<int, int64_t>> rec;
+    int64_t synced[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+
+    void push(const Op& o)
+    {
+        ops.push_back(o);
+        if (o.kind == kH2D || o.kind == kKernel || o.kind == kD2H) ++pos[o.stream];  // work, not markers
+    }
+    void emit_wait(int stream, int ev)
+    {
+        const auto r = rec[ev];
+        if (r.first == stream || synced[stream][r.first] >= r.second) return;
+        Op o; o.kind = kWait; o.stream = stream; o.event = ev; push(o);
+        synced[stream][r.first] = r.second;
+    }
+    void emit_record(int stream, int ev)
+    {
+        Op o; o.kind = kRecord; o.stream = stream; o.event = ev; push(o);
+        rec[ev] = {stream, pos[stream]};
+    }
+
+    int ensure(int mat, const Tag& tg, int64_t t, int lo, int n, int64_t i, int64_t j, int64_t kc)
+    {
+        for (int s = lo; s < lo + n; ++s)
+            if (content[s] == tg) { last_use[s] = t; return s; }
+        // victim: empty first, then farthest next use, then least recently used
+        int victim = -1;
+        int64_t vnext = -1, vlast = 0;
+        for (int s = lo; s < lo + n; ++s) {
+            if (content[s].m < 0) { victim = s; break; }
+            const int64_t nu = next_use(content[s], t);
+            if (victim < 0 || nu > vnext || (nu == vnext && last_use[s] < vlast)) {
+                victim = s; vnext = nu; vlast = last_use[s];
+            }
+        }
+        if (read_since_load[victim]) emit_wait(kStreamH2D, ev_free(p, victim));
+        Op o; o.kind = kH2D; o.stream = kStreamH2D; o.wslot = victim; o.wtag = tg;
+        o.i = i; o.j = j; o.kc = kc;
+        (void)mat;
+        push(o);
+        emit_record(kStreamH2D, ev_ready(p, victim));
+        content[victim] = tg;
+        last_use[victim] = t;
+        read_since_load[victim] = false;
+        compute_synced[victim] = false;
+        return victim;
+    }
+
+    void run()
+    {
+        const int a0 = 0, b0 = p.nA, c0 = p.nA + p.nB;
+        const bool have_k = p.K > 0;
+        for (int64_t j = 0; j < p.w; ++j)
+            for (int64_t i = 0; i < p.h; ++i) {
+                const int64_t blk = j * p.h + i;
+                const int sc = c0 + (int)(blk % p.nC);
+                for (int64_t kc = 0; kc < p.nkc; ++kc) {
+                    const int64_t t = step_index(i, j, kc);
+                    int sa = -1, sb = -1;
+                    if (have_k) {
+                        sa = ensure(kMatA, Tag{kMatA, i, kc, 0}, t, a0, p.nA, i, j, kc);
+                        sb = ensure(kMatB, Tag{kMatB, kc, j, 0}, t, b0, p.nB, i, j, kc);
+                    }
+                    if (kc == 0) {
+                        const Tag ct{kMatC, i, j, 0};
+                        if (p.beta_nz) {
+                            if (d2h_pending[sc]) emit_wait(kStreamH2D, ev_out(p, sc));
+                            Op o; o.kind = kH2D; o.stream = kStreamH2D; o.wslot = sc; o.wtag = ct;
+                            o.i = i; o.j = j; o.kc = 0;
+                            push(o);
+                            emit_record(kStreamH2D, ev_ready(p, sc));
+                            compute_synced[sc] = false;
+                        } else if (d2h_pending[sc]) {
+                            emit_wait(kStreamCompute, ev_out(p, sc));
+                        }
+                        d2h_pending[sc] = false;
+                        content[sc] = ct;
+                    }
+                    // wait for the inputs' loads, latest-issued first (it covers the earlier ones)
+                    std::vector<int> need;
+                    for (int s : {sa, sb, sc})
+                        if (s >= 0 && !compute_synced[s]) need.push_back(s);
+                    std::sort(need.begin(), need.end(), [&](int x, int y) {
+                        return rec[ev_ready(p, x)].second > rec[ev_ready(p, y)].second;
+                    });
+                    for (int s : need) {
+                        emit_wait(kStreamCompute, ev_ready(p, s));
+                        compute_synced[s] = true;
+                    }
+                    Op k; k.kind = kKernel; k.stream = kStreamCompute;
+                    k.i = i; k.j = j; k.kc = kc;
+                    k.first = (kc == 0); k.last = (kc == p.nkc - 1);
+                    if (sa >= 0) { k.rslot[k.nr] = sa; k.rtag[k.nr] = content[sa]; ++k.nr; }
+                    if (sb >= 0) { k.rslot[k.nr] = sb; k.rtag[k.nr] = content[sb]; ++k.nr; }
+                    if (kc > 0 || p.beta_nz) { k.rslot[k.nr] = sc; k.rtag[k.nr] = content[sc]; ++k.nr; }
+                    k.wslot = sc;
+                    k.wtag = Tag{kMatC, i, j, kc + 1};
+                    push(k);
+                    content[sc] = k.wtag;
+                    for (int s : {sa, sb}) {
+                        if (s < 0) continue;
+                        read_since_load[s] = true;
+                        emit_record(kStreamCompute, ev_free(p, s));
+                    }
+                    if (kc == p.nkc - 1) {
+                        emit_record(kStreamCompute, ev_done(p, sc));
+                        emit_wait(kStreamD2H, ev_done(p, sc));
+                        Op d; d.kind = kD2H; d.stream = kStreamD2H; d.nr = 1;
+                        d.rslot[0] = sc; d.rtag[0] = content[sc];
+                        d.i = i; d.j = j; d.kc = kc;
+                        push(d);
+                        emit_record(kStreamD2H, ev_out(p, sc));
+                        d2h_pending[sc] = true;
+                    }
+                }
+            }
+    }
+};
+
+}  // namespace
+
+void build_schedule(const Plan& plan, std::vector<Op>& ops)
+{
+    ops.clear();
+    ops.reserve((size_t)(plan.h * plan.w * plan.nkc * 12 + 16));
+    Gen g(plan, ops);
+    g.run();
+}
+
+}  // namespace ooc

@@ -1,0 +1,169 @@
+"""Host-side logic of the library, checked without a GPU.
+
+* the shared library loads and exports every function include/ooc.h declares;
+* the planner's paper mode equals the oracle's reading of the Section IV
+  partitioner (bit-exact integers), and every plan fits its budget;
+* every issued schedule satisfies the Section IV buffer-hazard rule, checked by
+  the oracle's timeline checker, and returns each C block exactly once.
+"""
+import itertools
+import os
+import re
+
+import pytest
+
+import paper_1808_05056_gb300 as P
+from oracle import partition, pipeline
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "ooc.h")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    P.build()
+    P.load()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ooc_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported():
+    lib = P.load()
+    names = declared_functions()
+    assert "ooc_dgemm" in names and "ooc_plan" in names
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(P.EXPORTS) <= set(names)
+
+
+def test_errors_are_named():
+    for code in range(0, -11, -1):
+        assert P.ooc_strerror(code) != "unknown status"
+
+
+def test_invalid_arguments_rejected_before_device():
+    assert P.ooc_dgemm("X", "N", 2, 2, 2, 1.0, 1, 2, 1, 2, 0.0, 1, 2, 1 << 20) == P.OOC_ERR_INVALID_ARG
+    assert P.ooc_dgemm("N", "N", 2, 2, 4, 1.0, 1, 3, 1, 2, 0.0, 1, 2, 1 << 20) == P.OOC_ERR_INVALID_ARG
+    assert P.ooc_dgemm("N", "N", -1, 2, 2, 1.0, 1, 2, 1, 2, 0.0, 1, 2, 1 << 20) == P.OOC_ERR_INVALID_ARG
+    assert P.ooc_dgemm("N", "N", 2, 2, 2, 1.0, None, 2, 1, 2, 0.0, 1, 2, 1 << 20) == P.OOC_ERR_INVALID_ARG
+    # empty problems are a no-op
+    assert P.ooc_dgemm("N", "N", 0, 5, 5, 1.0, None, 5, None, 5, 0.0, None, 5, 1 << 20) == P.OOC_OK
+
+
+def test_paper_mode_worked_example():
+    plan = P.ooc_plan(4, 4, 8, 8, 1, 44 * 8, P.make_opts(flags=P.OOC_PLAN_PAPER))
+    assert plan["blocks"] == 8 and (plan["mb"], plan["nb"], plan["kb"]) == (1, 2, 8)
+    assert (plan["depth"], plan["b_buffers"], plan["c_buffers"]) == (2, 1, 2)
+
+
+@pytest.mark.parametrize("M,N,K,mem", [(4, 4, 8, 44), (16, 16, 16, 200), (12, 18, 10, 150),
+                                       (32, 8, 64, 1000), (6, 6, 6, 108), (24, 36, 5, 300),
+                                       (30, 20, 7, 199), (9, 27, 81, 2000)])
+def test_paper_mode_matches_oracle_partitioner(M, N, K, mem):
+    hw = partition.partition(M, N, K, mem)
+    opts = P.make_opts(flags=P.OOC_PLAN_PAPER)
+    if hw is None:
+        with pytest.raises(P.OocError):
+            P.ooc_plan(M, N, K, 8, 1, mem * 8, opts)
+        return
+    plan = P.ooc_plan(M, N, K, 8, 1, mem * 8, opts)
+    assert (M // plan["mb"], N // plan["nb"]) == hw
+
+
+@pytest.mark.parametrize("M,N,K,es,budget,beta", [
+    (1024, 1024, 1024, 8, 4 << 20, 0), (1000, 700, 300, 8, 1 << 20, 1), (64, 64, 64, 8, 1 << 16, 1),
+    (32768, 32768, 32768, 8, 4 << 30, 1), (65536, 65536, 16384, 8, 16 << 30, 0),
+    (65536, 65536, 65536, 4, 8 << 30, 1), (5000, 3, 7000, 8, 2 << 20, 0), (3, 5000, 7000, 8, 2 << 20, 1)])
+def test_auto_plans_fit_and_count_traffic(M, N, K, es, budget, beta):
+    plan = P.ooc_plan(M, N, K, es, beta, budget)
+    assert 0 < plan["device_bytes"] <= budget
+    assert plan["mb"] >= 1 and plan["nb"] >= 1 and plan["kb"] >= 1
+    # traffic lower bounds: every operand crosses at least once, C comes back once
+    assert plan["h2d_bytes"] >= (M * K + K * N + (M * N if beta else 0)) * es
+    assert plan["d2h_bytes"] == M * N * es
+
+
+def test_budget_too_small():
+    with pytest.raises(P.OocError) as e:
+        P.ooc_plan(1024, 1024, 1024, 8, 0, 4096)
+    assert e.value.code == P.OOC_ERR_BUDGET
+
+
+def to_checker(ops):
+    """Library schedule entries -> the oracle checker's operation dicts."""
+    kinds = {0: "h2d", 1: "kernel", 2: "d2h", 3: "record", 4: "wait"}
+    out = []
+    for o in ops:
+        d = dict(kind=kinds[o["kind"]], stream=o["stream"])
+        if o["kind"] in (3, 4):
+            d["event"] = o["event"]
+        if o["write_slot"] >= 0:
+            d["writes"] = [(o["write_slot"], o["write_tag"])]
+        d["reads"] = list(zip(o["read_slot"], o["read_tag"]))
+        out.append(d)
+    return out
+
+
+def _expected_blocks(M, N, plan):
+    h = -(-M // plan["mb"])
+    w = -(-N // plan["nb"])
+    nkc = plan["steps"] // (h * w)
+    return h, w, nkc
+
+
+CASES = [
+    # (M, N, K, es, beta, budget, opts kwargs)
+    (4, 4, 8, 8, 1, 44 * 8, dict(flags=1)),
+    (4, 4, 8, 8, 0, 44 * 8, dict(flags=1)),
+    (12, 18, 10, 8, 1, 150 * 8, dict(flags=1)),
+    (1024, 1024, 1024, 8, 0, 4 << 20, {}),
+    (1000, 700, 300, 8, 1, 1 << 20, {}),
+    (300, 200, 170, 8, 1, 0, dict(mb=64, nb=64, kb=64, depth=2, c_buffers=2)),
+    (300, 200, 170, 8, 0, 0, dict(mb=128, nb=64, kb=64, depth=3, c_buffers=3)),
+    (256, 256, 512, 8, 1, 0, dict(mb=64, nb=128, kb=128, depth=2, c_buffers=2)),
+    (200, 130, 0, 8, 1, 1 << 20, {}),
+    (640, 64, 640, 8, 1, 0, dict(mb=64, nb=64, kb=640, depth=2, c_buffers=2)),
+]
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_issued_schedule_respects_the_hazard_rule(case):
+    M, N, K, es, beta, budget, kw = CASES[case]
+    opts = P.make_opts(**kw)
+    if budget == 0:
+        budget = 1 << 40
+    plan = P.ooc_plan(M, N, K, es, beta, budget, opts)
+    ops = P.ooc_schedule(M, N, K, es, beta, budget, opts)
+    chk = to_checker(ops)
+    assert pipeline.check(chk) == []
+    h, w, nkc = _expected_blocks(M, N, plan)
+    finals = sorted(t for _, t in pipeline.final_host_writes(chk))
+    assert finals == sorted((2, i, j, nkc) for i in range(h) for j in range(w))
+    # every kernel of block (i, j, kc) reads its own A and B chunks (when K > 0)
+    for o in ops:
+        if o["kind"] != 1:
+            continue
+        _, i, j, v = o["write_tag"]
+        kc = v - 1
+        tags = o["read_tag"]
+        if K > 0:
+            assert (0, i, kc, 0) in tags and (1, kc, j, 0) in tags
+        if kc > 0 or beta:
+            assert (2, i, j, kc) in tags
+
+
+def test_checker_catches_a_dropped_library_wait():
+    ops = P.ooc_schedule(300, 200, 170, 8, 1, 1 << 40,
+                         P.make_opts(mb=64, nb=64, kb=64, depth=2, c_buffers=2))
+    chk = to_checker(ops)
+    waits = [k for k, o in enumerate(chk) if o["kind"] == "wait"]
+    assert waits
+    caught = 0
+    for k in waits:
+        if pipeline.check(chk[:k] + chk[k + 1:]):
+            caught += 1
+    # every wait the library issues is needed
+    assert caught == len(waits)
