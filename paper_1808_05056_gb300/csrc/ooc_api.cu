@@ -14,6 +14,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -196,6 +197,16 @@ struct Operands {
     double alpha, beta;
 };
 
+// OOC_TRACE=<file>: append one CSV line per copy/kernel of each call with its
+// stream, block indices, bytes, host issue time and device start/end (ms from
+// the call's first event) -- the pipeline timeline of Section IV's Fig. 3.
+struct TraceRec {
+    int kind, stream;
+    int64_t i, j, kc;
+    double bytes, host_ms;
+    cudaEvent_t e0, e1;
+};
+
 // Resources of one call, released in the destructor after the streams drain.
 struct Exec {
     Plan p;
@@ -204,6 +215,7 @@ struct Exec {
     cudaStream_t st[3] = {nullptr, nullptr, nullptr};
     std::vector<cudaEvent_t> ev;
     std::vector<cudaEvent_t> kev;  // timing pairs around tile kernels
+    std::vector<TraceRec> trace;
     cudaEvent_t t_begin = nullptr, t_end[3] = {nullptr, nullptr, nullptr};
 
     Exec() = default;
@@ -217,6 +229,8 @@ struct Exec {
             if (s) cudaStreamSynchronize(s);
         for (auto& e : ev) { if (e) cudaEventDestroy(e); e = nullptr; }
         for (auto& e : kev) { if (e) cudaEventDestroy(e); e = nullptr; }
+        for (auto& r : trace) { if (r.e0) cudaEventDestroy(r.e0); if (r.e1) cudaEventDestroy(r.e1); }
+        trace.clear();
         if (t_begin) cudaEventDestroy(t_begin);
         t_begin = nullptr;
         for (auto& e : t_end) { if (e) cudaEventDestroy(e); e = nullptr; }
@@ -275,6 +289,7 @@ int run_ooc(char ta, char tb, int64_t M, int64_t N, int64_t K, const Operands& o
     std::memset(&opts, 0, sizeof(opts));
     if (opts_in) opts = *opts_in;
     PlanRequest rq{M, N, K, es, o.beta != 0.0, is_t(ta), is_t(tb), budget, opts};
+    rq.lda = o.lda; rq.ldb = o.ldb; rq.ldc = o.ldc;
     double hg = 0, dg = 0;
     if (ooc_query_device(nullptr, &hg, &dg) == OOC_OK && hg > 0 && dg > 0) {
         rq.h2d_gbps = hg;
@@ -322,8 +337,20 @@ int run_ooc(char ta, char tb, int64_t M, int64_t N, int64_t K, const Operands& o
     const char* hA = static_cast<const char*>(o.A);
     const char* hB = static_cast<const char*>(o.B);
     char* hC = static_cast<char*>(o.C);
+    const char* trace_path = std::getenv("OOC_TRACE");
+    const auto t_issue0 = std::chrono::steady_clock::now();
     for (const Op& op : ops) {
         cudaStream_t s = x.st[op.stream];
+        const bool traced = trace_path && (op.kind == kH2D || op.kind == kKernel || op.kind == kD2H);
+        if (traced) {
+            TraceRec r{op.kind, op.stream, op.i, op.j, op.kc, 0.0,
+                       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_issue0).count(),
+                       nullptr, nullptr};
+            CK(cudaEventCreate(&r.e0));
+            CK(cudaEventCreate(&r.e1));
+            CK(cudaEventRecord(r.e0, s));
+            x.trace.push_back(r);
+        }
         switch (op.kind) {
         case kRecord: CK(cudaEventRecord(x.ev[op.event], s)); break;
         case kWait: CK(cudaStreamWaitEvent(s, x.ev[op.event], 0)); break;
@@ -349,7 +376,10 @@ int run_ooc(char ta, char tb, int64_t M, int64_t N, int64_t K, const Operands& o
                 spitch = o.ldc * es; dpitch = p.ldc_dev * es;
             }
             if (rows > 0 && width > 0) {
-                CK(cudaMemcpy2DAsync(dst, dpitch, src, spitch, width * es, rows, cudaMemcpyHostToDevice, s));
+                if (spitch == width * es && dpitch == width * es)
+                    CK(cudaMemcpyAsync(dst, src, rows * width * es, cudaMemcpyHostToDevice, s));
+                else
+                    CK(cudaMemcpy2DAsync(dst, dpitch, src, spitch, width * es, rows, cudaMemcpyHostToDevice, s));
                 h2d += (double)rows * width * es;
             }
             break;
@@ -367,10 +397,18 @@ int run_ooc(char ta, char tb, int64_t M, int64_t N, int64_t K, const Operands& o
             const int64_t rows = p.rows_of(op.i), width = p.cols_of(op.j);
             char* dst = hC + (op.i * p.mb * o.ldc + op.j * p.nb) * es;
             const char* src = x.arena + slot_offset(p, op.rslot[0]);
-            CK(cudaMemcpy2DAsync(dst, o.ldc * es, src, p.ldc_dev * es, width * es, rows, cudaMemcpyDeviceToHost, s));
+            if (o.ldc == width && p.ldc_dev == width)
+                CK(cudaMemcpyAsync(dst, src, rows * width * es, cudaMemcpyDeviceToHost, s));
+            else
+                CK(cudaMemcpy2DAsync(dst, o.ldc * es, src, p.ldc_dev * es, width * es, rows, cudaMemcpyDeviceToHost,
+                                     s));
             d2h += (double)rows * width * es;
             break;
         }
+        }
+        if (traced) {
+            CK(cudaEventRecord(x.trace.back().e1, s));
+            x.trace.back().bytes = h2d + d2h;  // running total; differenced when written
         }
     }
     for (int i = 0; i < 3; ++i) CK(cudaEventRecord(x.t_end[i], x.st[i]));
@@ -378,6 +416,24 @@ int run_ooc(char ta, char tb, int64_t M, int64_t N, int64_t K, const Operands& o
     int herr = 0;
     CK(cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost));
     if (herr != 0) return fail(OOC_ERR_TIMEOUT, "a device-side wait gave up (status " + std::to_string(herr) + ")");
+    if (trace_path) {
+        if (FILE* f = std::fopen(trace_path, "a")) {
+            std::fprintf(f, "# call M=%lld N=%lld K=%lld mb=%lld nb=%lld kb=%lld nA=%d nB=%d nC=%d\n", (long long)M,
+                         (long long)N, (long long)K, (long long)p.mb, (long long)p.nb, (long long)p.kb, p.nA, p.nB,
+                         p.nC);
+            double prev = 0;
+            for (auto& r : x.trace) {
+                float a = 0, b = 0;
+                cudaEventElapsedTime(&a, x.t_begin, r.e0);
+                cudaEventElapsedTime(&b, x.t_begin, r.e1);
+                const char* k = r.kind == kH2D ? "h2d" : r.kind == kKernel ? "kernel" : "d2h";
+                std::fprintf(f, "%s,%d,%lld,%lld,%lld,%.0f,%.3f,%.3f,%.3f\n", k, r.stream, (long long)r.i,
+                             (long long)r.j, (long long)r.kc, r.bytes - prev, r.host_ms, a, b);
+                prev = r.bytes;
+            }
+            std::fclose(f);
+        }
+    }
 
     if (stats) {
         float ms = 0, best = 0;

@@ -22,6 +22,7 @@ struct Plan {
     bool beta_nz = false;
     bool ta = false, tb = false;
     bool paper = false;
+    int64_t lda_host = 0, ldb_host = 0, ldc_host = 0;  // 0: assume contiguous host rows
     int64_t mb = 0, nb = 0, kb = 0;
     int64_t h = 0, w = 0, nkc = 0;
     int32_t nA = 0, nB = 0, nC = 0;
@@ -49,6 +50,7 @@ struct PlanRequest {
     size_t budget;
     ooc_opts opts;
     double h2d_gbps = 200.0, d2h_gbps = 190.0;  // link model for the estimate
+    int64_t lda = 0, ldb = 0, ldc = 0;          // host leading dimensions (0: rows are contiguous)
 };
 
 // Returns OOC_OK and fills `plan`, or an error code with a message in `why`.

@@ -17,7 +17,7 @@
 // data is not overwritten until the kernels using it have completed): steps
 // run column-major over C blocks (j outer, i inner, the B slice of a column
 // stays resident as in Fig. 1's loop order), K chunks innermost.  Every load
-// picks its slot by farthest next use (ties: least recently used), waits on
+// takes an empty slot, else the least recently used one; it waits on
 // the event recorded after the slot's last reader, and records a ready event
 // that the compute stream waits on.  H2D, compute and D2H each have a stream.
 #include <algorithm>
@@ -108,6 +108,21 @@ void traffic(Plan& p)
     p.d2h_bytes = C;
 }
 
+// Host rows of one copy of `mat` are short and not contiguous.
+bool narrow_rows(const Plan& p, int mat)
+{
+    int64_t width, full, ld;
+    if (mat == kMatA) {
+        width = p.ta ? p.mb : p.kb; full = p.ta ? p.M : p.K; ld = p.lda_host;
+    } else if (mat == kMatB) {
+        width = p.tb ? p.kb : p.nb; full = p.tb ? p.K : p.N; ld = p.ldb_host;
+    } else {
+        width = p.nb; full = p.N; ld = p.ldc_host;
+    }
+    const bool contiguous = width == full && (ld == 0 || ld == full);
+    return !contiguous && width * p.es < 64 * 1024;
+}
+
 double estimate(const Plan& p, const FormModel& f, int sms, double h2d_gbps, double d2h_gbps)
 {
     const double slots_total = (double)sms * f.ctas_per_sm;
@@ -134,7 +149,18 @@ double estimate(const Plan& p, const FormModel& f, int sms, double h2d_gbps, dou
     double bubbles = 0;
     if (p.nB < 2 * p.nkc && p.nkc <= p.nB) bubbles = (double)(p.w - 1) * p.K * p.nb * es / bw_h;
     const double steps = (double)p.h * p.w * p.nkc;
-    return std::max(t_comp, t_link) + fill + drain + bubbles + steps * 8e-6;
+    // Strided host copies with short rows (< 64 KiB) run far below the link
+    // rate on this host link and were seen to slow down further as more host
+    // memory is touched; charge them at a quarter of the link rate, outside
+    // the overlap.
+    double narrow = 0;
+    const double A = (double)p.M * p.K * es, B = (double)p.K * p.N * es, C = (double)p.M * p.N * es;
+    const double a_loads = (p.h == 1 && p.nkc <= p.nA) ? A : A * p.w;
+    const double b_loads = (p.nkc <= p.nB) ? B : B * p.h;
+    if (narrow_rows(p, kMatA)) narrow += a_loads;
+    if (narrow_rows(p, kMatB)) narrow += b_loads;
+    if (narrow_rows(p, kMatC)) narrow += C * (p.beta_nz ? 2.0 : 1.0);
+    return std::max(t_comp, t_link) + fill + drain + bubbles + steps * 8e-6 + narrow / (0.25 * bw_h);
 }
 
 bool paper_plan(const PlanRequest& rq, Plan& best, std::string& why)
@@ -172,6 +198,7 @@ int make_plan(const PlanRequest& rq, Plan& p, std::string& why)
     p = Plan{};
     p.M = rq.M; p.N = rq.N; p.K = rq.K; p.es = rq.es;
     p.beta_nz = rq.beta_nz; p.ta = rq.ta; p.tb = rq.tb;
+    p.lda_host = rq.lda; p.ldb_host = rq.ldb; p.ldc_host = rq.ldc;
     int form = rq.opts.form;
     if (form == OOC_FORM_AUTO) form = (rq.es == 8) ? OOC_FORM_FP64 : OOC_FORM_BF16X3;
     if (rq.es == 8 && form != OOC_FORM_FP64 && form != OOC_FORM_OZAKI) {
@@ -313,29 +340,6 @@ struct Gen {
 
     int64_t step_index(int64_t i, int64_t j, int64_t kc) const { return (j * p.h + i) * p.nkc + kc; }
 
-    // next step (> t) that needs tile `tg`, or INT64_MAX
-    int64_t next_use(const Tag& tg, int64_t t) const
-    {
-        const int64_t INF = std::numeric_limits<int64_t>::max();
-        if (tg.m == kMatA) {  // (i, kc) used in every column
-            for (int64_t j = 0; j < p.w; ++j) {
-                int64_t s = step_index(tg.r, j, tg.c);
-                if (s > t) return s;
-            }
-            return INF;
-        }
-        if (tg.m == kMatB) {  // (kc, j) used by every row of column j
-            const int64_t j = tg.c, kc = tg.r;
-            const int64_t first = step_index(0, j, kc), last = step_index(p.h - 1, j, kc);
-            if (t < first) return first;
-            if (t >= last) return INF;
-            // the current row's step if this chunk comes later in it, else the next row's
-            const int64_t i_cur = (t / p.nkc) - j * p.h;
-            return step_index(i_cur, j, kc) > t ? step_index(i_cur, j, kc) : step_index(i_cur + 1, j, kc);
-        }
-        return INF;
-    }
-
     // Stream-order bookkeeping: pos[s] counts copies/kernels issued on stream s;
     // rec[e] is (stream, position) of event e's latest record; synced[a][b]
     // is the last position of stream b that stream a is already ordered
@@ -366,15 +370,17 @@ struct Gen {
     {
         for (int s = lo; s < lo + n; ++s)
             if (content[s] == tg) { last_use[s] = t; return s; }
-        // victim: empty first, then farthest next use, then least recently used
+        // victim: an empty slot, else the least recently used one.  LRU keeps
+        // the victim's last reader as old as possible, so the load overlaps the
+        // kernels in between; cyclic reuse longer than the ring is reloaded,
+        // which is what the planner's traffic model counts.
         int victim = -1;
-        int64_t vnext = -1, vlast = 0;
-        for (int s = lo; s < lo + n; ++s) {
+        for (int s = lo; s < lo + n; ++s)
             if (content[s].m < 0) { victim = s; break; }
-            const int64_t nu = next_use(content[s], t);
-            if (victim < 0 || nu > vnext || (nu == vnext && last_use[s] < vlast)) {
-                victim = s; vnext = nu; vlast = last_use[s];
-            }
+        if (victim < 0) {
+            victim = lo;
+            for (int s = lo + 1; s < lo + n; ++s)
+                if (last_use[s] < last_use[victim]) victim = s;
         }
         if (read_since_load[victim]) emit_wait(kStreamH2D, ev_free(p, victim));
         Op o; o.kind = kH2D; o.stream = kStreamH2D; o.wslot = victim; o.wtag = tg;

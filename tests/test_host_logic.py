@@ -167,3 +167,33 @@ def test_checker_catches_a_dropped_library_wait():
             caught += 1
     # every wait the library issues is needed
     assert caught == len(waits)
+
+
+@pytest.mark.parametrize("M,N,K,es,beta,budget,kw", [
+    (32768, 32768, 32768, 8, 1, 4 << 30, {}),
+    (1000, 700, 300, 8, 1, 0, dict(mb=64, nb=64, kb=64, depth=2, c_buffers=2)),
+    (4096, 4096, 4096, 8, 0, 0, dict(mb=1024, nb=1024, kb=1024, depth=3, c_buffers=2)),
+])
+def test_operand_loads_never_wait_for_the_kernel_just_issued(M, N, K, es, beta, budget, kw):
+    """With rings of >= 2 slots, a refill waits at most for the kernel two steps back,
+    so every copy overlaps the kernel issued just before it."""
+    budget = budget or 1 << 40
+    opts = P.make_opts(**kw)
+    plan = P.ooc_plan(M, N, K, es, beta, budget, opts)
+    assert plan["depth"] >= 2
+    ops = P.ooc_schedule(M, N, K, es, beta, budget, opts)
+    kernels_issued = 0
+    recorded_after = {}      # event -> kernels issued when it was last recorded (compute stream)
+    pending_wait = None
+    for o in ops:
+        if o["kind"] == 1:
+            kernels_issued += 1
+        elif o["kind"] == 3 and o["stream"] == 1:
+            recorded_after[o["event"]] = kernels_issued
+        elif o["kind"] == 4 and o["stream"] == 0:
+            pending_wait = o["event"]
+        elif o["kind"] == 0:
+            if pending_wait is not None and pending_wait in recorded_after and o["write_tag"][0] in (0, 1):
+                waited_kernel = recorded_after[pending_wait] - 1
+                assert waited_kernel <= kernels_issued - 2, (o["write_tag"], waited_kernel, kernels_issued)
+            pending_wait = None
