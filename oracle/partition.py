@@ -1,15 +1,16 @@
 """The matrix partitioner of Section IV, read literally (oracle; test infrastructure only).
 
-Section IV: hclMatrixPartitioner splits A (M x K) into h equal horizontal
-slices, B (K x N) into w equal vertical slices and C into h x w equal blocks,
-so that the data needed to update any two blocks of C in the same column fits
-in the device memory dMemSize (counted in elements).
+Section IV: the partitioner cuts A (M x K) into h horizontal slices of equal
+size, B (K x N) into w vertical slices of equal size and C into the h x w
+blocks between them, choosing h and w so that everything needed to update two
+C blocks that share a block column is resident in the device memory dMemSize
+at the same time (sizes counted in elements).
 
-Reading (the paper states the constraint, not the search):
-  * "two blocks of C in the same column" (i and i+1 of column j) need two A
-    slices, the one B slice of that column and two C blocks:
+Reading (the paper gives the constraint, not the search):
+  * two C blocks of one column (rows i and i+1 of column j) need two A slices,
+    the single B slice of the column and the two C blocks:
         2 * (M/h) * K + K * (N/w) + 2 * (M/h) * (N/w) <= dMemSize;
-  * "equal" slices: h divides M and w divides N;
+  * equal sizes: h divides M and w divides N;
   * among the (h, w) that fit, the fewest blocks h * w; ties go to the smaller
     footprint, then to the larger h.
 The worked example of Section IV (A 4 x 8, B 8 x 4, C 4 x 4, 44 elements,

@@ -5,9 +5,9 @@
 // pipeline fit the device budget.  Two modes:
 //   * paper mode reproduces the Section IV partitioner: h | M, w | N equal
 //     slices, whole-K slices, buffers for two A slices, one B slice and two C
-//     blocks ("any two blocks of C in the same column"), fewest blocks first,
-//     then the smaller footprint, then the larger h (the worked example's
-//     4 x 2 split of Fig. 2);
+//     blocks (enough to update two C blocks of one block column), fewest
+//     blocks first, then the smaller footprint, then the larger h (the worked
+//     example's 4 x 2 split of Fig. 2);
 //   * auto mode searches block rows/columns, an optional K chunk and the
 //     buffer counts, scoring each candidate with a time estimate built from
 //     the device's compute rate, tile-wave quantisation and the measured host
