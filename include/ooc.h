@@ -135,6 +135,29 @@ int ooc_dgemm_device(char transA, char transB, int64_t M, int64_t N, int64_t K, 
                      double* dC, int64_t ldc, void* stream);
 
 /*
+ * No-allocation variant of ooc_dgemm.  The paper has no counterpart: this entry
+ * point is for callers that cannot call cudaMalloc -- a process whose device
+ * memory is owned by another allocator (for example a framework's caching
+ * allocator that has reserved the pool), or a latency-bound caller that cannot
+ * take the device-wide synchronisation of cudaFree.  It allocates nothing: the
+ * device buffers are carved from one fixed array of OOC_NOALLOC_MAX_BYTES
+ * (32 MiB) in the library's device memory, which every GPU that loads the
+ * library holds until the process exits; it creates no streams or events and
+ * issues all copies and tile kernels, in order, on `stream` (a cudaStream_t,
+ * NULL = legacy default stream), so copies do not overlap the kernels.
+ * Arguments are those of ooc_dgemm (FP64, plain FP64 form, pinned host
+ * operands) with device_budget_bytes <= OOC_NOALLOC_MAX_BYTES, else
+ * OOC_ERR_INVALID_ARG.  The call is synchronous.  The first call on a device
+ * (that device current) looks up the array's address; make it before any
+ * stream capture.  All calls share the array and it keeps the last call's
+ * contents; calls that overlap on the GPU race, so serialise them.
+ */
+#define OOC_NOALLOC_MAX_BYTES (32u << 20)
+int ooc_dgemm_noalloc(char transA, char transB, int64_t M, int64_t N, int64_t K, double alpha,
+                      const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
+                      double* C, int64_t ldc, size_t device_budget_bytes, void* stream);
+
+/*
  * Plan only (host, no device needed): the block/chunk/buffer plan the call
  * with these arguments would use.  elem_bytes is 8 for ooc_dgemm, 4 for
  * ooc_sgemm.  Fills stats' plan fields (mb, nb, kb, depth, c_buffers,

@@ -168,6 +168,21 @@ def ooc_dgemm_device(transA, transB, M, N, K, alpha, dA, lda, dB, ldb, beta, dC,
                                 ldb, beta, _ptr(dC), ldc, stream)
 
 
+def ooc_dgemm_noalloc(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, budget, stream=None):
+    """C ABI ooc_dgemm_noalloc (no device allocation; budget <= OOC_NOALLOC_MAX_BYTES); returns the status."""
+    lib = load()
+    f = lib.ooc_dgemm_noalloc
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_char, ctypes.c_char, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
+                  ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_double,
+                  ctypes.c_void_p, ctypes.c_int64, ctypes.c_size_t, ctypes.c_void_p]
+    return f(transA.encode(), transB.encode(), M, N, K, alpha, _ptr(A), lda, _ptr(B), ldb, beta, _ptr(C), ldc,
+             budget, stream)
+
+
+OOC_NOALLOC_MAX_BYTES = 32 << 20
+
+
 def ooc_plan(M, N, K, elem_bytes, beta_nonzero, budget, opts=None):
     """C ABI ooc_plan; returns the plan as a dict (raises on error)."""
     lib = load()
