@@ -95,6 +95,28 @@ int encode_map_2d(void* map_out, int dtype, const void* base, uint64_t inner, ui
     return OOC_OK;
 }
 
+int encode_map_3d_bf16(void* map_out, const void* base, uint64_t inner, uint64_t rows, uint64_t planes,
+                       uint32_t box_inner, uint32_t box_rows, std::string& why)
+{
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) {
+        why = "cuTensorMapEncodeTiled unavailable";
+        return OOC_ERR_CUDA;
+    }
+    cuuint64_t dims[3] = {inner, rows, planes};
+    cuuint64_t strides[2] = {inner * 2, inner * rows * 2};
+    cuuint32_t box[3] = {box_inner, box_rows, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(reinterpret_cast<CUtensorMap*>(map_out), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
+                    const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        why = "cuTensorMapEncodeTiled (3-D bf16) failed (" + std::to_string((int)r) + ")";
+        return OOC_ERR_CUDA;
+    }
+    return OOC_OK;
+}
+
 }  // namespace ooc
 
 using namespace ooc;
@@ -216,6 +238,7 @@ struct Exec {
     std::vector<cudaEvent_t> ev;
     std::vector<cudaEvent_t> kev;  // timing pairs around tile kernels
     std::vector<TraceRec> trace;
+    std::vector<int64_t> gen, split_gen;  // loads into each slot / loads already split (split forms)
     cudaEvent_t t_begin = nullptr, t_end[3] = {nullptr, nullptr, nullptr};
 
     Exec() = default;
@@ -248,6 +271,90 @@ struct Exec {
         if (e_ != cudaSuccess) return fail(OOC_ERR_CUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
     } while (0)
 
+// Tensor-core forms: split each newly loaded A / B slot into bf16 planes (once
+// per load), then run the split-product tile kernel on the C block.
+int launch_split_tile(const Plan& p, const Op& op, Exec& x, const Operands& o, int sa, int sb, int sc,
+                      std::string& why)
+{
+    const bool ozaki = p.form == OOC_FORM_OZAKI;
+    const int S = split_planes(p);
+    const int64_t rows = p.rows_of(op.i), cols = p.cols_of(op.j), K = p.K;
+    const int64_t k_pad = split_k_pad(p);
+    const int64_t ra_pad = split_rows_pad(p.mb), rb_pad = split_rows_pad(p.nb);
+    int* err = reinterpret_cast<int*>(x.arena);
+    void* st = x.st[kStreamCompute];
+    struct Side {
+        int slot;
+        bool is_a;
+    } sides[2] = {{sa, true}, {sb, false}};
+    int* exps[2] = {nullptr, nullptr};
+    char* planes[2] = {nullptr, nullptr};
+    for (int q = 0; q < 2; ++q) {
+        const int s = sides[q].slot;
+        if (s < 0) continue;
+        char* aux = x.arena + slot_aux_offset(p, s);
+        const int64_t rpad = sides[q].is_a ? ra_pad : rb_pad;
+        planes[q] = aux;
+        exps[q] = reinterpret_cast<int*>(aux + split_planes_bytes(p, sides[q].is_a ? p.mb : p.nb));
+        if (x.split_gen[s] == x.gen[s]) continue;
+        const int nrows = (int)(sides[q].is_a ? rows : cols);
+        // element (r, k) of the slot: K-major rows or K down the stored rows
+        const bool kmajor = sides[q].is_a ? !p.ta : p.tb;
+        const int64_t ld = sides[q].is_a ? p.lda_dev : p.ldb_dev;
+        const int64_t sr = kmajor ? ld : 1, sk = kmajor ? 1 : ld;
+        const char* src = x.arena + slot_offset(p, s);
+        int rc;
+        if (ozaki) {
+            auto* rowmax = reinterpret_cast<unsigned long long*>(
+                reinterpret_cast<char*>(exps[q]) + ((rpad * 4 + 255) / 256) * 256);
+            rc = launch_split_ozaki(reinterpret_cast<const double*>(src), sr, sk, nrows, (int)K, (int)rpad,
+                                    (int)k_pad, S, kOzakiBeta, planes[q], exps[q], rowmax, st, why);
+        } else {
+            rc = launch_split_bf16x3(reinterpret_cast<const float*>(src), sr, sk, nrows, (int)K, (int)rpad, (int)k_pad,
+                                     planes[q], st, why);
+        }
+        if (rc) return rc;
+        x.split_gen[s] = x.gen[s];
+    }
+    TcProblem P;
+    P.M = rows; P.N = cols; P.k_pad = K > 0 ? k_pad : 0;
+    P.chunk = ozaki ? kOzakiChunk : kBf16x3Chunk;
+    P.a_planes = planes[0]; P.a_rows_pad = ra_pad; P.a_nplanes = S;
+    P.b_planes = planes[1]; P.b_rows_pad = rb_pad; P.b_nplanes = S;
+    if (ozaki) {
+        int n = 0;
+        for (int d = 2; d <= S + 1; ++d)
+            for (int s1 = 1; s1 < d; ++s1) {
+                const int t1 = d - s1;
+                if (s1 > S || t1 > S) continue;
+                TcGroupSpec& g = P.groups[n++];
+                g.na = 1; g.nb = 1; g.np = 1;
+                g.aplane[0] = s1 - 1; g.bplane[0] = t1 - 1;
+                g.pa[0] = 0; g.pb[0] = 0;
+                g.scale_exp = -kOzakiBeta * d;
+            }
+        P.ngroups = n;
+        P.row_exp = exps[0];
+        P.col_exp = exps[1];
+    } else {
+        TcGroupSpec& g = P.groups[0];
+        g.na = 3; g.nb = 3; g.np = 6;
+        for (int i = 0; i < 3; ++i) { g.aplane[i] = i; g.bplane[i] = i; }
+        const int pa[6] = {0, 0, 1, 0, 1, 2}, pb[6] = {0, 1, 0, 2, 1, 0};  // hh hm mh hl mm lh
+        for (int i = 0; i < 6; ++i) { g.pa[i] = pa[i]; g.pb[i] = pb[i]; }
+        P.ngroups = 1;
+        P.df32 = true;
+    }
+    P.alpha = o.alpha;
+    P.beta = op.first ? o.beta : 1.0;
+    P.read_c = !op.first || o.beta != 0.0;
+    P.c_fp32 = p.es == 4;
+    P.C = x.arena + slot_offset(p, sc);
+    P.ldc = p.ldc_dev;
+    P.err = err;
+    return launch_tc_terms(P, st, why);
+}
+
 int launch_tile(const Plan& p, const Op& op, Exec& x, const Operands& o, std::string& why)
 {
     const int sa = op.nr > 0 && op.rslot[0] < p.nA ? op.rslot[0] : -1;
@@ -259,6 +366,7 @@ int launch_tile(const Plan& p, const Op& op, Exec& x, const Operands& o, std::st
     const double beta_eff = op.first ? o.beta : 1.0;
     const bool read_c = !op.first || o.beta != 0.0;
     int* err = reinterpret_cast<int*>(x.arena);
+    if (p.form == OOC_FORM_BF16X3 || p.form == OOC_FORM_OZAKI) return launch_split_tile(p, op, x, o, sa, sb, sc, why);
     if (p.form == OOC_FORM_FP64) {
         const double* dA = sa >= 0 ? reinterpret_cast<const double*>(x.arena + slot_offset(p, sa)) : nullptr;
         const double* dB = sb >= 0 ? reinterpret_cast<const double*>(x.arena + slot_offset(p, sb)) : nullptr;
@@ -317,6 +425,8 @@ int run_ooc(char ta, char tb, int64_t M, int64_t N, int64_t K, const Operands& o
         x.own_arena = true;
     }
     for (auto& s : x.st) CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    x.gen.assign(p.slots(), 0);
+    x.split_gen.assign(p.slots(), -1);
     x.ev.resize(n_events(p), nullptr);
     for (auto& e : x.ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     int64_t nkern = 0;
@@ -358,6 +468,7 @@ int run_ooc(char ta, char tb, int64_t M, int64_t N, int64_t K, const Operands& o
             if (inj.copy >= 0 && n_copy++ == inj.copy) return fail(OOC_ERR_INJECTED, "injected copy failure");
             const Tag& t = op.wtag;
             char* dst = x.arena + slot_offset(p, op.wslot);
+            ++x.gen[op.wslot];
             const char* src;
             int64_t rows, width, spitch, dpitch;
             if (t.m == kMatA) {

@@ -88,6 +88,13 @@ inline int32_t n_events(const Plan& p) { return 4 * p.slots(); }
 
 void build_schedule(const Plan& plan, std::vector<Op>& ops);
 
+// split-form scratch of a slot (bf16 planes, Ozaki exponents) -- plan.cpp
+int split_planes(const Plan& p);
+int64_t split_rows_pad(int64_t rows);
+int64_t split_k_pad(const Plan& p);
+size_t split_planes_bytes(const Plan& p, int64_t rows);
+size_t split_aux_bytes(const Plan& p, int64_t rows);
+
 // slot byte offsets inside the arena
 size_t slot_offset(const Plan& p, int32_t slot);
 size_t slot_aux_offset(const Plan& p, int32_t slot);
@@ -105,6 +112,52 @@ int launch_fp64_tile(bool a_kmajor, bool b_kmajor, int64_t M, int64_t N, int64_t
                      const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
                      bool read_c, double* C, int64_t ldc, int* err, void* stream,
                      std::string& why);
+
+// --- tensor-core split-product forms (tc_gemm.cu) -------------------------
+// A group: pairs (A plane, B plane) accumulated into one FP32 TMEM accumulator
+// and added into FP64 with weight 2^scale_exp after every K chunk.
+struct TcGroupSpec {
+    int na = 0, nb = 0, np = 0;
+    int aplane[4] = {0, 0, 0, 0}, bplane[4] = {0, 0, 0, 0};  // planes loaded per K block
+    int pa[6] = {0, 0, 0, 0, 0, 0}, pb[6] = {0, 0, 0, 0, 0, 0};  // pair -> loaded A / B index
+    int scale_exp = 0;
+};
+
+struct TcProblem {
+    int64_t M = 0, N = 0, k_pad = 0;  // C block rows / cols, padded K (multiple of 64)
+    int chunk = 0;                     // K elements per FP64 flush (multiple of 64)
+    const void* a_planes = nullptr;    // [a_nplanes][a_rows_pad][k_pad] bf16
+    int64_t a_rows_pad = 0;
+    int a_nplanes = 0;
+    const void* b_planes = nullptr;    // [b_nplanes][b_rows_pad][k_pad] bf16 (rows = C columns)
+    int64_t b_rows_pad = 0;
+    int b_nplanes = 0;
+    int ngroups = 0;
+    TcGroupSpec groups[64];
+    double alpha = 1.0, beta = 0.0;
+    bool read_c = false, c_fp32 = false;
+    void* C = nullptr;
+    int64_t ldc = 0;
+    const int* row_exp = nullptr;      // per-row power-of-two scale (Ozaki), nullable
+    const int* col_exp = nullptr;
+    int* err = nullptr;
+    bool df32 = false;                 // two accumulators per group, double-float drain (BF16x3)
+};
+
+int tc_max_groups();
+int launch_tc_terms(const TcProblem& P, void* stream, std::string& why);
+int launch_split_bf16x3(const float* X, int64_t sr, int64_t sk, int rows, int K, int rows_pad, int k_pad,
+                        void* planes, void* stream, std::string& why);
+int launch_split_ozaki(const double* X, int64_t sr, int64_t sk, int rows, int K, int rows_pad, int k_pad, int S,
+                       int beta, void* planes, int* rowexp, unsigned long long* rowmax, void* stream,
+                       std::string& why);
+int encode_map_3d_bf16(void* map_out, const void* base, uint64_t inner, uint64_t rows, uint64_t planes,
+                       uint32_t box_inner, uint32_t box_rows, std::string& why);
+
+// Ozaki digit width and the largest K chunk whose digit products sum exactly in FP32
+constexpr int kOzakiBeta = 6;
+constexpr int kOzakiChunk = 4096;
+constexpr int kBf16x3Chunk = 128;
 
 int device_sm_count();
 void set_error(const std::string& msg);

@@ -45,8 +45,6 @@ struct FormModel {
     int ctas_per_sm;
     int products;            // slice products per logical product
     int slices;
-    double aux_a, aux_b;     // extra device bytes per element of an A / B slot (split planes)
-    double aux_c;            // extra device bytes per C element (FP64 accumulator etc.)
 };
 
 FormModel form_model(int form, int es, int64_t K, int slices_opt)
@@ -58,18 +56,35 @@ FormModel form_model(int form, int es, int64_t K, int slices_opt)
     } else if (form == OOC_FORM_BF16X3) {
         f.tile_m = 128; f.tile_n = 128; f.ctas_per_sm = 1;
         f.products = 6; f.slices = 3;
-        f.rate = 1.5e15 / 6.0;
-        f.aux_a = 3 * 2; f.aux_b = 3 * 2; f.aux_c = 8;
+        f.rate = 1.2e15 / 6.0;
     } else {  // Ozaki
         int s = slices_opt > 0 ? slices_opt : 8;
         f.tile_m = 128; f.tile_n = 128; f.ctas_per_sm = 1;
         f.slices = s; f.products = s * (s + 1) / 2;
-        f.rate = 1.5e15 / f.products;
-        f.aux_a = 2.0 * s + 0.0; f.aux_b = 2.0 * s; f.aux_c = 0;
+        f.rate = 1.2e15 / f.products;
     }
     (void)es; (void)K;
     return f;
 }
+
+}  // namespace
+
+int split_planes(const Plan& p) { return p.form == OOC_FORM_BF16X3 ? 3 : p.slices; }
+int64_t split_rows_pad(int64_t rows) { return round_up(std::max<int64_t>(rows, 1), 128); }
+int64_t split_k_pad(const Plan& p) { return round_up(p.kb, 64); }
+size_t split_planes_bytes(const Plan& p, int64_t rows)
+{
+    return align_up((size_t)split_planes(p) * split_rows_pad(rows) * split_k_pad(p) * 2, kAlign);
+}
+size_t split_aux_bytes(const Plan& p, int64_t rows)
+{
+    size_t b = split_planes_bytes(p, rows);
+    if (p.form == OOC_FORM_OZAKI)
+        b += align_up((size_t)split_rows_pad(rows) * 4, kAlign) + align_up((size_t)split_rows_pad(rows) * 8, kAlign);
+    return b;
+}
+
+namespace {
 
 void layout(Plan& p, const FormModel& f)
 {
@@ -83,14 +98,13 @@ void layout(Plan& p, const FormModel& f)
     p.b_slot = align_up((size_t)std::max<int64_t>(b_rows, 1) * p.ldb_dev * p.es, kAlign);
     const int es_c = p.es;  // C slot holds the host element type
     p.c_slot = align_up((size_t)p.mb * p.ldc_dev * es_c, kAlign);
-    p.a_aux = align_up((size_t)std::ceil(f.aux_a * (double)p.mb * (double)round_up(p.kb, 64)), kAlign);
-    p.b_aux = align_up((size_t)std::ceil(f.aux_b * (double)p.nb * (double)round_up(p.kb, 64)), kAlign);
-    p.c_aux = (p.nkc > 1 || p.es == 4) ? align_up((size_t)std::ceil(f.aux_c * (double)p.mb * (double)p.nb), kAlign) : 0;
-    if (p.form == OOC_FORM_OZAKI) {
-        // per-row / per-column exponents of the slot (int32 each)
-        p.a_aux += align_up((size_t)p.mb * 4, kAlign);
-        p.b_aux += align_up((size_t)p.nb * 4, kAlign);
+    p.a_aux = p.b_aux = p.c_aux = 0;
+    if (p.form != OOC_FORM_FP64) {
+        // bf16 planes [planes][rows_pad][k_pad], plus per-row exponent and max (Ozaki)
+        p.a_aux = split_aux_bytes(p, p.mb);
+        p.b_aux = split_aux_bytes(p, p.nb);
     }
+    (void)f;
     p.device_bytes = p.header + (size_t)p.nA * (p.a_slot + p.a_aux) +
                      (size_t)p.nB * (p.b_slot + p.b_aux) + (size_t)p.nC * (p.c_slot + p.c_aux);
 }
@@ -247,7 +261,8 @@ int make_plan(const PlanRequest& rq, Plan& p, std::string& why)
     const std::vector<int64_t> mbs = sizes(rq.M, f.tile_m, rq.opts.mb);
     const std::vector<int64_t> nbs = sizes(rq.N, f.tile_n, rq.opts.nb);
     std::vector<int64_t> kbs;
-    if (rq.opts.kb > 0) kbs.push_back(std::min<int64_t>(rq.opts.kb, std::max<int64_t>(rq.K, 1)));
+    if (form != OOC_FORM_FP64) kbs.push_back(std::max<int64_t>(rq.K, 1));  // split forms: whole-K slices
+    else if (rq.opts.kb > 0) kbs.push_back(std::min<int64_t>(rq.opts.kb, std::max<int64_t>(rq.K, 1)));
     else {
         kbs.push_back(std::max<int64_t>(rq.K, 1));
         for (int64_t c = 2; c <= 1024 && rq.K > 64; c = c < 8 ? c + 1 : c * 2) {
