@@ -39,7 +39,12 @@ CONFIGS = {
     # name: (form, M, N, K, alpha, beta, budget bytes, distribution)
     "fp64-32768": ("fp64", 32768, 32768, 32768, 1.5, 0.5, 4 << 30, synth.NORMAL),
     "fp64-1024": ("fp64", 1024, 1024, 1024, 1.0, 0.0, 4 << 20, synth.UNIFORM),
+    "ozaki-65536": ("ozaki", 65536, 65536, 16384, 1.0, 0.0, 16 << 30, synth.LOGSPREAD),
+    "bf16x3-65536": ("bf16x3", 65536, 65536, 65536, 1.0, 1.0, 8 << 30, synth.UNIFORM),
 }
+# per form: (element dtype name, relative Frobenius tolerance, products per logical product, dtype tag)
+FORMS = {"fp64": ("float64", 1e-13, 1, "f64"), "ozaki": ("float64", 1e-12, 36, "f64 (bf16 digit planes)"),
+         "bf16x3": ("float32", 1e-6, 6, "f32 (bf16x3 pieces)")}
 NOMINAL_FP64_TF, NOMINAL_BF16_TF = 1.25, 2250.0
 
 
@@ -60,17 +65,20 @@ def parse():
 def workload(args):
     form, M, N, K, alpha, beta, budget, dist = CONFIGS[args.config]
     if args.n:
-        M = N = K = args.n
+        K = max(1, K * args.n // M)
+        M = N = args.n
     if args.budget_gib:
         budget = int(args.budget_gib * (1 << 30))
     return dict(form=form, M=M, N=N, K=K, alpha=alpha, beta=beta, budget=budget, dist=dist)
 
 
 def config_json(w, l2_note):
-    dist = {synth.NORMAL: "N(0,1)", synth.UNIFORM: "U[-1,1]"}[w["dist"]]
-    return {"workload": "out-of-core %s GEMM M=N=K=%d, alpha=%g beta=%g, %s, host pinned %.0f GiB, "
-                        "device budget %.2f GiB" % (w["form"].upper(), w["M"], w["alpha"], w["beta"], dist,
-                                                    3 * w["M"] * w["N"] * 8 / 2 ** 30, w["budget"] / 2 ** 30),
+    dist = {synth.NORMAL: "N(0,1)", synth.UNIFORM: "U[-1,1]", synth.LOGSPREAD: "sign*10^U(-4,4)"}[w["dist"]]
+    es = 4 if w["form"] == "bf16x3" else 8
+    host = (w["M"] * w["K"] + w["K"] * w["N"] + w["M"] * w["N"]) * es
+    return {"workload": "out-of-core %s GEMM M=%d N=%d K=%d, alpha=%g beta=%g, %s, host pinned %.0f GiB, "
+                        "device budget %.2f GiB" % (w["form"].upper(), w["M"], w["N"], w["K"], w["alpha"], w["beta"],
+                                                    dist, host / 2 ** 30, w["budget"] / 2 ** 30),
             "M": w["M"], "N": w["N"], "K": w["K"], "alpha": w["alpha"], "beta": w["beta"],
             "device_budget_bytes": w["budget"], "form": w["form"], "l2": l2_note}
 
@@ -112,7 +120,7 @@ def host_cores():
 def calibrate_sample(w, A, B, C, target_s, r, nthreads):
     """Number of r x r blocks the oracle computes in about target_s seconds (at least 2)."""
     blocks = sample_blocks(w, 1, r, seed=999)
-    cold = [C[i:i + r, j:j + r].numpy().copy() for i, j in blocks]
+    cold = [C[i:i + r, j:j + r].numpy().astype(np.float64) for i, j in blocks]
     _, dt, _ = oracle_sample(w, A, B, cold, blocks, r, nthreads)
     return max(2, min(256, int(target_s / max(dt, 1e-3))))
 
@@ -185,14 +193,15 @@ def run_reference(args, w, world, rank, pg):
     import torch
     r = 64
     cores = host_cores()
-    A = torch.empty((w["M"], w["K"]), dtype=torch.float64)
-    B = torch.empty((w["K"], w["N"]), dtype=torch.float64)
-    C = torch.empty((w["M"], w["N"]), dtype=torch.float64)
+    dt = getattr(torch, FORMS[w["form"]][0])
+    A = torch.empty((w["M"], w["K"]), dtype=dt)
+    B = torch.empty((w["K"], w["N"]), dtype=dt)
+    C = torch.empty((w["M"], w["N"]), dtype=dt)
     for t, s in ((A, 0), (B, 1), (C, 2)):
         synth.fill(t, 1, s, w["dist"])
     per_step = max(1, calibrate_sample(w, A, B, C, args.cpu_seconds / max(1, args.steps + args.warmup), r, cores))
     blocks = sample_blocks(w, per_step, r)
-    cold = [C[i:i + r, j:j + r].numpy().copy() for i, j in blocks]
+    cold = [C[i:i + r, j:j + r].numpy().astype(np.float64) for i, j in blocks]
     for _ in range(args.warmup):
         oracle_sample(w, A, B, cold, blocks, r, cores)
     times = []
@@ -206,7 +215,7 @@ def run_reference(args, w, world, rank, pg):
     line = {"impl": "reference", "metric": "out-of-core GEMM effective TFLOP/s incl. transfers",
             "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Philox)",
+            "vs_baseline": None, "dtype": FORMS[w["form"]][3], "data": "synthetic (seeded Philox)",
             "config": config_json(w, "CPU oracle"),
             "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -220,19 +229,23 @@ def run_ours(args, w, world, rank, local, pg):
     torch.cuda.set_device(local)
     P.load()
     M, N, K = w["M"], w["N"], w["K"]
-    A = torch.empty((M, K), dtype=torch.float64, pin_memory=True)
-    B = torch.empty((K, N), dtype=torch.float64, pin_memory=True)
-    C = torch.empty((M, N), dtype=torch.float64, pin_memory=True)
+    dtname, tol, products, dtag = FORMS[w["form"]]
+    dt = getattr(torch, dtname)
+    A = torch.empty((M, K), dtype=dt, pin_memory=True)
+    B = torch.empty((K, N), dtype=dt, pin_memory=True)
+    C = torch.empty((M, N), dtype=dt, pin_memory=True)
     t_fill = time.perf_counter()
     for t, s in ((A, 0), (B, 1), (C, 2)):
         synth.fill(t, 1 + rank, s, w["dist"])
     t_fill = time.perf_counter() - t_fill
-    opts = P.make_opts(form=P.OOC_FORM_FP64)
+    form_id = {"fp64": P.OOC_FORM_FP64, "ozaki": P.OOC_FORM_OZAKI, "bf16x3": P.OOC_FORM_BF16X3}[w["form"]]
+    opts = P.make_opts(form=form_id)
+    call = P.ooc_sgemm if w["form"] == "bf16x3" else P.ooc_dgemm
 
     def step():
         st = P.ooc_stats()
         t0 = time.perf_counter()
-        rc = P.ooc_dgemm("N", "N", M, N, K, w["alpha"], A, K, B, N, w["beta"], C, N, w["budget"], opts, st)
+        rc = call("N", "N", M, N, K, w["alpha"], A, K, B, N, w["beta"], C, N, w["budget"], opts, st)
         wall = time.perf_counter() - t0
         if rc != 0:
             raise RuntimeError("ooc_dgemm failed: %s: %s" % (P.ooc_strerror(rc), P.ooc_last_error()))
@@ -245,7 +258,7 @@ def run_ours(args, w, world, rank, local, pg):
     blocks = sample_blocks(w, n_blocks, r)
     for k in range(max(0, args.warmup - 1)):
         step()
-    cold = [C[i:i + r, j:j + r].numpy().copy() for i, j in blocks]
+    cold = [C[i:i + r, j:j + r].numpy().astype(np.float64) for i, j in blocks]
     step()
     parity = None
     cpu = None
@@ -255,8 +268,8 @@ def run_ours(args, w, world, rank, local, pg):
         for (i, j), rv in zip(blocks, ref):
             got = C[i:i + r, j:j + r].numpy()
             errs.append(float(np.linalg.norm(got - rv) / np.linalg.norm(rv)))
-        parity = {"max_rel_fro": max(errs), "tolerance": 1e-13, "blocks": len(blocks), "block": r,
-                  "pass": max(errs) <= 1e-13}
+        parity = {"max_rel_fro": max(errs), "tolerance": tol, "blocks": len(blocks), "block": r,
+                  "pass": max(errs) <= tol}
         cpu = {"value": 2.0 * r * r * K * len(blocks) / dt / 1e12, "unit": "TFLOP/s", "cores": used,
                "kind": "oracle",
                "sample": "%d seeded %dx%d blocks of C, K=%d, %.1f s (full problem extrapolated at this rate)" % (
@@ -290,7 +303,7 @@ def run_ours(args, w, world, rank, local, pg):
     dev_s = sum(s.device_seconds for s, _ in stats)
     wall_s = sum(wl for _, wl in stats)
     ker_s = sum(s.kernel_seconds for s, _ in stats)
-    launches = sum(s.steps for s, _ in stats)
+    launches = sum(s.kernel_launches for s, _ in stats)
     if pg:
         import torch.distributed as dist
         t = torch.tensor([dev_s, wall_s], dtype=torch.float64, device="cuda")
@@ -302,35 +315,48 @@ def run_ours(args, w, world, rank, local, pg):
     value = world * flops * args.steps / dev_s / 1e12
     e2e = world * flops * args.steps / wall_s / 1e12
     pk, pk_src = peaks()
-    fp64_peak = pk["bf16_tflops_sustained"] * NOMINAL_FP64_TF / NOMINAL_BF16_TF
-    achieved = flops * args.steps / ker_s / 1e12
     s0 = stats[0][0]
     link_h2d, link_d2h = P.ooc_query_device()[1:]
     b_alg = s0.h2d_bytes + s0.d2h_bytes
-    t_roof = max(flops / (fp64_peak * 1e12), s0.h2d_bytes / (link_h2d * 1e9), s0.d2h_bytes / (link_d2h * 1e9))
+    if w["form"] == "fp64":
+        peak = pk["bf16_tflops_sustained"] * NOMINAL_FP64_TF / NOMINAL_BF16_TF
+        achieved = flops * args.steps / ker_s / 1e12
+        roof = {"bound": "tensor", "kernel": "fp64_tile_kernel (FP64 mma.sync, TMA-fed)",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": "%s bf16 sustained %.1f TF x nominal FP64/BF16 ratio %.2f/%.0f" % (
+                    pk_src, pk["bf16_tflops_sustained"], NOMINAL_FP64_TF, NOMINAL_BF16_TF),
+                "fp64_cublas_measured_tflops": cublas_tf, "frac_of_cublas_dgemm": achieved / cublas_tf,
+                "launches_per_step": s0.steps}
+        compute_peak = peak
+    else:
+        peak = pk["bf16_tflops_sustained"]
+        achieved = flops * s0.products * args.steps / ker_s / 1e12
+        roof = {"bound": "tensor",
+                "kernel": "tc_terms_kernel (tcgen05 bf16 x bf16 -> f32 TMEM, TMA) with its split kernels",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "flop_count": "2*M*N*K x %d bf16 products per logical product" % s0.products,
+                "peak_source": "%s bf16 sustained (cuBLAS) %.1f TF" % (pk_src, peak),
+                "logical_tflops": flops * args.steps / ker_s / 1e12, "launches_per_step": s0.steps}
+        compute_peak = peak / s0.products
+    t_roof = max(flops / (compute_peak * 1e12), s0.h2d_bytes / (link_h2d * 1e9), s0.d2h_bytes / (link_d2h * 1e9))
+    host_gib = (M * K + K * N + M * N) * (4 if w["form"] == "bf16x3" else 8) / 2 ** 30
     line = {
         "metric": "out-of-core GEMM effective TFLOP/s incl. transfers",
         "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * dev_s / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Philox N(0,1), pinned host)",
-        "config": config_json(w, "inputs larger than L2: 24 GiB host operands streamed through a 4 GiB "
-                                 "device budget each step"),
-        "roofline": {"bound": "tensor", "kernel": "fp64_tile_kernel (FP64 mma.sync, TMA-fed)",
-                     "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
-                     "traffic": None,
-                     "peak_source": "%s bf16 sustained %.1f TF x nominal FP64/BF16 ratio %.2f/%.0f" % (
-                         pk_src, pk["bf16_tflops_sustained"], NOMINAL_FP64_TF, NOMINAL_BF16_TF),
-                     "fp64_cublas_measured_tflops": cublas_tf,
-                     "frac_of_cublas_dgemm": achieved / cublas_tf,
-                     "launches_per_step": s0.steps},
+        "vs_baseline": None, "dtype": dtag, "data": "synthetic (seeded Philox, pinned host)",
+        "config": config_json(w, "inputs larger than L2: %.0f GiB host operands streamed through a %.2f GiB "
+                                 "device budget each step" % (host_gib, w["budget"] / 2 ** 30)),
+        "roofline": roof,
         "ooc_roofline": {"t_roof_s": t_roof, "t_step_s": dev_s / args.steps, "frac": t_roof / (dev_s / args.steps),
-                         "fp64_peak_tflops": fp64_peak, "h2d_gbps": link_h2d, "d2h_gbps": link_d2h,
+                         "compute_peak_logical_tflops": compute_peak, "h2d_gbps": link_h2d, "d2h_gbps": link_d2h,
                          "h2d_bytes": s0.h2d_bytes, "d2h_bytes": s0.d2h_bytes, "bytes_alg": b_alg},
         "plan": {"mb": s0.mb, "nb": s0.nb, "kb": s0.kb, "depth": s0.depth, "b_buffers": s0.b_buffers,
                  "c_buffers": s0.c_buffers, "blocks": s0.blocks, "device_bytes": s0.device_bytes},
         "e2e": {"value": e2e, "unit": "TFLOP/s", "h2d_bytes_per_step": s0.h2d_bytes,
                 "d2h_bytes_per_step": s0.d2h_bytes},
         "gpu_launches": launches,
+        "fp64_cublas_measured_tflops": cublas_tf,
         "parity": parity,
         "cpu_baseline": cpu,
         "clocks": clocks,

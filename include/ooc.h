@@ -100,6 +100,7 @@ typedef struct {
     int64_t device_bytes;    /* device buffer bytes the plan uses                    */
     int32_t slices;          /* Ozaki slices / BF16x3 pieces used                    */
     int32_t products;        /* slice products per tile                              */
+    int64_t kernel_launches; /* kernels the call launched (tile + split kernels)    */
 } ooc_stats;
 
 /*

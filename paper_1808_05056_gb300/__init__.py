@@ -44,7 +44,8 @@ class ooc_stats(ctypes.Structure):
                 ("mb", ctypes.c_int64), ("nb", ctypes.c_int64), ("kb", ctypes.c_int64),
                 ("depth", ctypes.c_int32), ("c_buffers", ctypes.c_int32), ("b_buffers", ctypes.c_int32),
                 ("form", ctypes.c_int32), ("blocks", ctypes.c_int64), ("steps", ctypes.c_int64),
-                ("device_bytes", ctypes.c_int64), ("slices", ctypes.c_int32), ("products", ctypes.c_int32)]
+                ("device_bytes", ctypes.c_int64), ("slices", ctypes.c_int32), ("products", ctypes.c_int32),
+                ("kernel_launches", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -109,7 +109,8 @@ int encode_map_3d_bf16(void* map_out, const void* base, uint64_t inner, uint64_t
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = fn(reinterpret_cast<CUtensorMap*>(map_out), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
                     const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                    box_inner * 2 == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         why = "cuTensorMapEncodeTiled (3-D bf16) failed (" + std::to_string((int)r) + ")";
         return OOC_ERR_CUDA;
@@ -239,6 +240,7 @@ struct Exec {
     std::vector<cudaEvent_t> kev;  // timing pairs around tile kernels
     std::vector<TraceRec> trace;
     std::vector<int64_t> gen, split_gen;  // loads into each slot / loads already split (split forms)
+    int64_t launches = 0;                 // kernels launched by this call
     cudaEvent_t t_begin = nullptr, t_end[3] = {nullptr, nullptr, nullptr};
 
     Exec() = default;
@@ -304,6 +306,7 @@ int launch_split_tile(const Plan& p, const Op& op, Exec& x, const Operands& o, i
         const int64_t sr = kmajor ? ld : 1, sk = kmajor ? 1 : ld;
         const char* src = x.arena + slot_offset(p, s);
         int rc;
+        x.launches += ozaki ? (K > 0 ? 3 : 2) : 1;
         if (ozaki) {
             auto* rowmax = reinterpret_cast<unsigned long long*>(
                 reinterpret_cast<char*>(exps[q]) + ((rpad * 4 + 255) / 256) * 256);
@@ -322,16 +325,20 @@ int launch_split_tile(const Plan& p, const Op& op, Exec& x, const Operands& o, i
     P.a_planes = planes[0]; P.a_rows_pad = ra_pad; P.a_nplanes = S;
     P.b_planes = planes[1]; P.b_rows_pad = rb_pad; P.b_nplanes = S;
     if (ozaki) {
+        // digit products (s, t) with s + t <= S + 1, two consecutive t per group
+        // so that the group loads the A plane s once
         int n = 0;
-        for (int d = 2; d <= S + 1; ++d)
-            for (int s1 = 1; s1 < d; ++s1) {
-                const int t1 = d - s1;
-                if (s1 > S || t1 > S) continue;
+        for (int s1 = 1; s1 <= S; ++s1)
+            for (int t1 = 1; t1 <= S + 1 - s1; t1 += 2) {
                 TcGroupSpec& g = P.groups[n++];
-                g.na = 1; g.nb = 1; g.np = 1;
-                g.aplane[0] = s1 - 1; g.bplane[0] = t1 - 1;
+                const bool two = t1 + 1 <= S + 1 - s1;
+                g.na = 1; g.nb = two ? 2 : 1; g.np = two ? 2 : 1;
+                g.aplane[0] = s1 - 1;
+                g.bplane[0] = t1 - 1; g.bplane[1] = two ? t1 : 0;
                 g.pa[0] = 0; g.pb[0] = 0;
-                g.scale_exp = -kOzakiBeta * d;
+                g.pa[1] = 0; g.pb[1] = 1;
+                g.scale_exp = -kOzakiBeta * (s1 + t1);
+                g.scale_exp2 = -kOzakiBeta * (s1 + t1 + 1);
             }
         P.ngroups = n;
         P.row_exp = exps[0];
@@ -352,6 +359,8 @@ int launch_split_tile(const Plan& p, const Op& op, Exec& x, const Operands& o, i
     P.C = x.arena + slot_offset(p, sc);
     P.ldc = p.ldc_dev;
     P.err = err;
+    P.kblock = 64;
+    ++x.launches;
     return launch_tc_terms(P, st, why);
 }
 
@@ -371,6 +380,7 @@ int launch_tile(const Plan& p, const Op& op, Exec& x, const Operands& o, std::st
         const double* dA = sa >= 0 ? reinterpret_cast<const double*>(x.arena + slot_offset(p, sa)) : nullptr;
         const double* dB = sb >= 0 ? reinterpret_cast<const double*>(x.arena + slot_offset(p, sb)) : nullptr;
         double* dC = reinterpret_cast<double*>(x.arena + slot_offset(p, sc));
+        ++x.launches;
         return launch_fp64_tile(!p.ta, p.tb, rows, cols, kk, o.alpha, dA, p.lda_dev, dB, p.ldb_dev, beta_eff, read_c,
                                 dC, p.ldc_dev, err, x.st[kStreamCompute], why);
     }
@@ -566,6 +576,7 @@ int run_ooc(char ta, char tb, int64_t M, int64_t N, int64_t K, const Operands& o
         stats->blocks = p.h * p.w; stats->steps = p.h * p.w * p.nkc;
         stats->device_bytes = (int64_t)p.device_bytes;
         stats->slices = p.slices; stats->products = p.products;
+        stats->kernel_launches = x.launches;
     }
     // release before taking the wall time (the arena free is part of the call)
     x.release();

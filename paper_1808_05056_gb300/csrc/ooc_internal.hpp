@@ -120,7 +120,8 @@ struct TcGroupSpec {
     int na = 0, nb = 0, np = 0;
     int aplane[4] = {0, 0, 0, 0}, bplane[4] = {0, 0, 0, 0};  // planes loaded per K block
     int pa[6] = {0, 0, 0, 0, 0, 0}, pb[6] = {0, 0, 0, 0, 0, 0};  // pair -> loaded A / B index
-    int scale_exp = 0;
+    int scale_exp = 0;   // weight of pair 0's accumulator
+    int scale_exp2 = 0;  // weight of the second accumulator (exact form: pair 1)
 };
 
 struct TcProblem {
@@ -142,6 +143,7 @@ struct TcProblem {
     const int* col_exp = nullptr;
     int* err = nullptr;
     bool df32 = false;                 // two accumulators per group, double-float drain (BF16x3)
+    int kblock = 64;                   // K block per pipeline stage: 64 or 32
 };
 
 int tc_max_groups();

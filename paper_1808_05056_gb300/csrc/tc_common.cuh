@@ -3,9 +3,10 @@
 // descriptor, tcgen05.mma / commit / ld, and 3-D TMA tile loads.
 //
 // Conventions used by every kernel that includes this file:
-//   * operand tiles are K-major bf16, 64 elements (128 bytes) of K per row,
-//     written by TMA with the 128-byte swizzle; a tile of R rows occupies
-//     R * 128 bytes and starts on a 1024-byte boundary (8-row swizzle atoms);
+//   * operand tiles are K-major bf16 written by TMA with the 128-byte swizzle
+//     (64 elements of K per row, 1024-byte 8-row atoms) or the 64-byte swizzle
+//     (32 elements of K per row, 512-byte atoms); tiles start on a 1024-byte
+//     boundary;
 //   * the MMA is cta_group::1 with M = 128, so accumulator row i lives in
 //     TMEM lane i and column j in TMEM column (base + j), 32-bit each.
 #pragma once
@@ -31,6 +32,19 @@ __device__ __forceinline__ uint64_t sw128_kmajor_desc(uint32_t smem_addr)
     d |= (uint64_t)(1024 >> 4) << 32;
     d |= (uint64_t)1 << 46;
     d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// Same for the 64-byte swizzle (32 bf16 of K per row): 8-row atom pitch 512 B,
+// layout code 4.
+__device__ __forceinline__ uint64_t sw64_kmajor_desc(uint32_t smem_addr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((smem_addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(512 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)4 << 61;
     return d;
 }
 

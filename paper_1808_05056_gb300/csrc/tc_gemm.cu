@@ -20,19 +20,20 @@
 //   2^(-beta (s+t)), and the epilogue applies 2^(e_i + f_j), alpha and beta.
 //
 // Kernel shape (both forms): persistent CTAs, one per SM, tile 128 x 128.
-//   warp 0      TMA producer: for each (tile, K chunk, group, 64-wide K block)
-//               loads the group's bf16 plane tiles (128 rows x 64 K, 128-byte
-//               swizzle) into a ring of shared-memory stages;
-//   warp 1      allocates 256 TMEM columns and issues tcgen05.mma (M=128,
-//               N=128, K=16) for every pair of the group into one of two TMEM
-//               accumulators, committing stage releases and accumulator-full
+//   warp 0      TMA producer: for each (tile, K chunk, group, K block of 64
+//               or 32) loads the group's bf16 plane tiles (128 rows x the K
+//               block, 128- or 64-byte swizzle) into a ring of stages;
+//   warp 1      allocates all 512 TMEM columns (two buffers x two 128-column
+//               accumulators) and issues tcgen05.mma (M=128, N=128, K=16):
+//               pair 0 of the group into accumulator 0, the other pairs into
+//               accumulator 1, committing stage releases and buffer-full
 //               events to mbarriers;
 //   warps 2-17  epilogue: read a finished accumulator with tcgen05.ld, add it
 //               (times the group weight) into FP64 (Ozaki) or double-float
 //               FP32 (BF16x3) registers, 32 columns per warp, release it, and
 //               after the last chunk write alpha*acc*2^(e_i+f_j) + beta*C_old.
-// The two accumulators let the tensor cores run the next group while the
-// epilogue drains the previous one.  Every wait is bounded (device_sync.cuh).
+// The two buffers let the tensor cores run the next group while the epilogue
+// drains the previous one.  Every wait is bounded (device_sync.cuh).
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -49,8 +50,7 @@ namespace ooc {
 
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 64;
-constexpr uint32_t TILE_BYTES = 128u * BK * 2u;  // one plane tile: 128 rows x 64 bf16
+constexpr int BM = 128, BN = 128;
 constexpr uint32_t RING_BYTES = 192u * 1024u;
 constexpr int EPI_WARPS = 16;            // 4 per TMEM lane quadrant, 32 columns each
 constexpr int THREADS = (2 + EPI_WARPS) * 32;
@@ -63,8 +63,9 @@ struct TcGroup {
     int8_t bplane[4];
     int8_t pa[6];
     int8_t pb[6];
-    int16_t scale_exp;
-    int16_t pad1[3];
+    int16_t scale_exp;   // weight of accumulator 0 (pair 0)
+    int16_t scale_exp2;  // weight of accumulator 1 (pairs 1.., Ozaki)
+    int16_t pad1[2];
 };
 static_assert(sizeof(TcGroup) == 32, "group record layout");
 
@@ -90,14 +91,17 @@ struct TcArgs {
 // double-float (hi, lo) FP32 pair per output with TwoSum; the tensor cores
 // round their FP32 accumulator toward zero, so each accumulator add is biased
 // by up to one ulp and the leading product must not absorb the small ones.
-// DF32 = false (Ozaki): one accumulator per group, exact integer partial sums,
-// drained into FP64 with the group's power-of-two weight.
-template <bool DF32>
+// DF32 = false (Ozaki): each of the group's (at most two) pairs has its own
+// accumulator of exact integer partial sums, drained into FP64 with its
+// power-of-two weight; the two pairs share the A digit plane.
+// BK: K block of one stage, 64 (128-byte swizzle) or 32 (64-byte swizzle) bf16.
+template <bool DF32, int BK>
 __global__ void __launch_bounds__(THREADS, 1) tc_terms_kernel(const __grid_constant__ CUtensorMap tmA,
                                                               const __grid_constant__ CUtensorMap tmB,
                                                               const __grid_constant__ TcArgs p)
 {
-    constexpr uint32_t kAccCols = DF32 ? 2 * BN : BN;  // TMEM columns of one buffer
+    constexpr uint32_t TILE_BYTES = 128u * BK * 2u;  // one plane tile: 128 rows x BK bf16
+    constexpr uint32_t kAccCols = 2 * BN;  // TMEM columns of one buffer: accumulators 0 and 1
     constexpr uint32_t kTmemCols = 2 * kAccCols;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* ring = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -204,12 +208,13 @@ __global__ void __launch_bounds__(THREADS, 1) tc_terms_kernel(const __grid_const
                             for (int q = 0; q < g.np; ++q) {
                                 const uint32_t a0 = st + (uint32_t)g.pa[q] * TILE_BYTES;
                                 const uint32_t b0 = st + (uint32_t)(g.na + g.pb[q]) * TILE_BYTES;
-                                const bool second = DF32 && q > 0;
+                                const bool second = q > 0;
                                 const uint32_t d = second ? d_tmem + BN : d_tmem;
 #pragma unroll
                                 for (int k = 0; k < BK / 16; ++k) {
-                                    tc_mma_bf16(d, sw128_kmajor_desc(a0 + k * 32), sw128_kmajor_desc(b0 + k * 32),
-                                                idesc, second ? accumulate2 : accumulate);
+                                    const uint64_t da = BK == 64 ? sw128_kmajor_desc(a0 + k * 32) : sw64_kmajor_desc(a0 + k * 32);
+                                    const uint64_t db = BK == 64 ? sw128_kmajor_desc(b0 + k * 32) : sw64_kmajor_desc(b0 + k * 32);
+                                    tc_mma_bf16(d, da, db, idesc, second ? accumulate2 : accumulate);
                                     if (second) accumulate2 = 1; else accumulate = 1;
                                 }
                             }
@@ -275,7 +280,9 @@ __global__ void __launch_bounds__(THREADS, 1) tc_terms_kernel(const __grid_const
                             }
                         }
                     } else {
-                        const double wgt = ldexp(1.0, (int)p.g[gi].scale_exp);
+                        const double w0 = ldexp(1.0, (int)p.g[gi].scale_exp);
+                        const double w1 = ldexp(1.0, (int)p.g[gi].scale_exp2);
+                        const bool has_second = p.g[gi].np > 1;
 #pragma unroll
                         for (int cc = 0; cc < 2; ++cc) {
                             uint32_t v[16];
@@ -283,7 +290,14 @@ __global__ void __launch_bounds__(THREADS, 1) tc_terms_kernel(const __grid_const
                             tmem_wait_ld();
 #pragma unroll
                             for (int j = 0; j < 16; ++j)
-                                acc[cc * 16 + j] = fma((double)__uint_as_float(v[j]), wgt, acc[cc * 16 + j]);
+                                acc[cc * 16 + j] = fma((double)__uint_as_float(v[j]), w0, acc[cc * 16 + j]);
+                            if (has_second) {
+                                tmem_ld_32x32b_x16(t0 + BN + cc * 16, v);
+                                tmem_wait_ld();
+#pragma unroll
+                                for (int j = 0; j < 16; ++j)
+                                    acc[cc * 16 + j] = fma((double)__uint_as_float(v[j]), w1, acc[cc * 16 + j]);
+                            }
                         }
                     }
                     tc_fence_before();
@@ -498,13 +512,19 @@ int launch_tc_terms(const TcProblem& P, void* stream, std::string& why)
     if (P.M <= 0 || P.N <= 0) return OOC_OK;
     if (P.ngroups <= 0 || P.ngroups > MAX_GROUPS) { why = "bad group count"; return OOC_ERR_INVALID_ARG; }
     std::call_once(g_attr_once, [] {
-        cudaFuncSetAttribute(tc_terms_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
-        cudaFuncSetAttribute(tc_terms_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+        cudaFuncSetAttribute(tc_terms_kernel<true, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+        cudaFuncSetAttribute(tc_terms_kernel<false, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
         g_sms = device_sm_count();
     });
+    // 64-wide K blocks (128-byte swizzle) measured faster than 32-wide ones for
+    // both forms on GB300 (BF16x3 166 vs 136, Ozaki 28 vs 18 logical TFLOP/s)
+    const int BK = 64;
+    if (P.kblock != BK) { why = "only 64-wide K blocks are built"; return OOC_ERR_INVALID_ARG; }
+    const uint32_t TILE_BYTES = 128u * (uint32_t)BK * 2u;
     TcArgs a;
     std::memset(&a, 0, sizeof(a));
     a.M = (int)P.M; a.N = (int)P.N;
+    if (P.k_pad % BK || P.chunk % BK) { why = "K padding / chunk not a multiple of the K block"; return OOC_ERR_INVALID_ARG; }
     a.kblocks = (int)(P.k_pad / BK);
     a.chunk_kblocks = std::max(1, P.chunk / BK);
     a.nchunks = (a.kblocks + a.chunk_kblocks - 1) / a.chunk_kblocks;
@@ -523,10 +543,15 @@ int launch_tc_terms(const TcProblem& P, void* stream, std::string& why)
         for (int i = 0; i < 4; ++i) { d.aplane[i] = (int8_t)s.aplane[i]; d.bplane[i] = (int8_t)s.bplane[i]; }
         for (int i = 0; i < 6; ++i) { d.pa[i] = (int8_t)s.pa[i]; d.pb[i] = (int8_t)s.pb[i]; }
         d.scale_exp = (int16_t)s.scale_exp;
+        d.scale_exp2 = (int16_t)s.scale_exp2;
+        if (!P.df32 && s.np > 2) {
+            why = "exact (Ozaki) groups hold at most two pairs";
+            return OOC_ERR_INVALID_ARG;
+        }
         max_tiles = std::max(max_tiles, s.na + s.nb);
     }
     a.stage_bytes = (uint32_t)max_tiles * TILE_BYTES;
-    a.nstages = std::min<int>(16, (int)(RING_BYTES / a.stage_bytes));
+    a.nstages = std::min<int>(16, (int)(RING_BYTES / a.stage_bytes));  // barrier slots: 16
     if (a.nstages < 2) { why = "stage ring too small"; return OOC_ERR_INVALID_ARG; }
     a.alpha = P.alpha; a.beta = P.beta;
     a.read_c = P.read_c ? 1 : 0; a.c_fp32 = P.c_fp32 ? 1 : 0;
@@ -546,10 +571,9 @@ int launch_tc_terms(const TcProblem& P, void* stream, std::string& why)
         if (rc) return rc;
     }
     const int grid = std::min(a.tiles, g_sms > 0 ? g_sms : 152);
-    if (P.df32)
-        tc_terms_kernel<true><<<grid, THREADS, SMEM_BYTES, static_cast<cudaStream_t>(stream)>>>(ma, mb, a);
-    else
-        tc_terms_kernel<false><<<grid, THREADS, SMEM_BYTES, static_cast<cudaStream_t>(stream)>>>(ma, mb, a);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (P.df32) tc_terms_kernel<true, 64><<<grid, THREADS, SMEM_BYTES, st>>>(ma, mb, a);
+    else tc_terms_kernel<false, 64><<<grid, THREADS, SMEM_BYTES, st>>>(ma, mb, a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) { why = std::string("tc_terms launch: ") + cudaGetErrorString(e); return OOC_ERR_CUDA; }
     return OOC_OK;
