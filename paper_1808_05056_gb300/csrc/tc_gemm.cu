@@ -73,7 +73,7 @@ struct TcArgs {
     int M, N;
     int kblocks, chunk_kblocks, nchunks;
     int ngroups;
-    int tiles_n, tiles;
+    int tiles_m, tiles_n, tiles;
     int nstages;
     uint32_t stage_bytes;
     double alpha, beta;
@@ -85,6 +85,31 @@ struct TcArgs {
     int* err;
     TcGroup g[MAX_GROUPS];
 };
+
+// Tile order: groups of kRasterRows tile rows, column-major inside a group, so
+// that the ~152 tiles in flight at once span few rows and few columns and
+// share their A and B plane tiles in L2.
+constexpr int kRasterRows = 8;
+__device__ __forceinline__ void tile_coords(int tile, int tiles_m, int tiles_n, int& tm, int& tn)
+{
+    const int per_group = kRasterRows * tiles_n;
+    const int g = tile / per_group, r = tile % per_group;
+    const int first = g * kRasterRows;
+    const int rows = min(tiles_m - first, kRasterRows);
+    tm = first + r % rows;
+    tn = r / rows;
+}
+
+// Exact FP32 integer x (|x| < 2^24) times 2^e as a double, built from the bit
+// fields with integer operations (no conversion or multiply on the FP64 pipe).
+__device__ __forceinline__ double scaled_f32_to_f64(uint32_t xb, int e)
+{
+    if ((xb & 0x7FFFFFFFu) == 0u) return 0.0;
+    const uint64_t sign = (uint64_t)(xb >> 31) << 63;
+    const uint64_t ex = (uint64_t)((int)((xb >> 23) & 0xFFu) - 127 + 1023 + e) << 52;
+    const uint64_t man = (uint64_t)(xb & 0x7FFFFFu) << 29;
+    return __longlong_as_double((long long)(sign | ex | man));
+}
 
 // DF32 = true (BF16x3): the first pair of a group (the leading product) and the
 // other pairs use two separate TMEM accumulators, drained into an unbiased
@@ -146,7 +171,8 @@ __global__ void __launch_bounds__(THREADS, 1) tc_terms_kernel(const __grid_const
             bool ok = true;
             for (int64_t tl = 0; tl < my_tiles && ok; ++tl) {
                 const int tile = (int)blockIdx.x + (int)tl * (int)gridDim.x;
-                const int tm = tile / p.tiles_n, tn = tile % p.tiles_n;
+                int tm, tn;
+                tile_coords(tile, p.tiles_m, p.tiles_n, tm, tn);
                 for (int c = 0; c < p.nchunks && ok; ++c) {
                     const int kb0 = c * p.chunk_kblocks, kb1 = min(p.kblocks, kb0 + p.chunk_kblocks);
                     for (int gi = 0; gi < p.ngroups && ok; ++gi) {
@@ -247,7 +273,8 @@ __global__ void __launch_bounds__(THREADS, 1) tc_terms_kernel(const __grid_const
         bool ok = true;
         for (int64_t tl = 0; tl < my_tiles && ok; ++tl) {
             const int tile = (int)blockIdx.x + (int)tl * (int)gridDim.x;
-            const int tm = tile / p.tiles_n, tn = tile % p.tiles_n;
+            int tm, tn;
+            tile_coords(tile, p.tiles_m, p.tiles_n, tm, tn);
             for (int c = 0; c < p.nchunks && ok; ++c) {
                 for (int gi = 0; gi < p.ngroups; ++gi, ++unit) {
                     const int buf = (int)(unit & 1u);
@@ -280,8 +307,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_terms_kernel(const __grid_const
                             }
                         }
                     } else {
-                        const double w0 = ldexp(1.0, (int)p.g[gi].scale_exp);
-                        const double w1 = ldexp(1.0, (int)p.g[gi].scale_exp2);
+                        const int e0 = p.g[gi].scale_exp, e1 = p.g[gi].scale_exp2;
                         const bool has_second = p.g[gi].np > 1;
 #pragma unroll
                         for (int cc = 0; cc < 2; ++cc) {
@@ -289,14 +315,12 @@ __global__ void __launch_bounds__(THREADS, 1) tc_terms_kernel(const __grid_const
                             tmem_ld_32x32b_x16(t0 + cc * 16, v);
                             tmem_wait_ld();
 #pragma unroll
-                            for (int j = 0; j < 16; ++j)
-                                acc[cc * 16 + j] = fma((double)__uint_as_float(v[j]), w0, acc[cc * 16 + j]);
+                            for (int j = 0; j < 16; ++j) acc[cc * 16 + j] += scaled_f32_to_f64(v[j], e0);
                             if (has_second) {
                                 tmem_ld_32x32b_x16(t0 + BN + cc * 16, v);
                                 tmem_wait_ld();
 #pragma unroll
-                                for (int j = 0; j < 16; ++j)
-                                    acc[cc * 16 + j] = fma((double)__uint_as_float(v[j]), w1, acc[cc * 16 + j]);
+                                for (int j = 0; j < 16; ++j) acc[cc * 16 + j] += scaled_f32_to_f64(v[j], e1);
                             }
                         }
                     }
@@ -530,7 +554,8 @@ int launch_tc_terms(const TcProblem& P, void* stream, std::string& why)
     a.nchunks = (a.kblocks + a.chunk_kblocks - 1) / a.chunk_kblocks;
     a.ngroups = P.ngroups;
     a.tiles_n = (int)((P.N + BN - 1) / BN);
-    a.tiles = (int)((P.M + BM - 1) / BM) * a.tiles_n;
+    a.tiles_m = (int)((P.M + BM - 1) / BM);
+    a.tiles = a.tiles_m * a.tiles_n;
     int max_tiles = 0;
     for (int g = 0; g < P.ngroups; ++g) {
         const TcGroupSpec& s = P.groups[g];
