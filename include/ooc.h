@@ -125,6 +125,39 @@ int ooc_sgemm(char transA, char transB, int64_t M, int64_t N, int64_t K, float a
               float* C, int64_t ldc, size_t device_budget_bytes, const ooc_opts* opts,
               ooc_stats* stats);
 
+/* One GEMM of a batch: the arguments of ooc_dgemm for one problem. */
+typedef struct {
+    char transA, transB;
+    char reserved[6];
+    int64_t M, N, K;
+    double alpha, beta;
+    const double* A;
+    int64_t lda;
+    const double* B;
+    int64_t ldb;
+    double* C;
+    int64_t ldc;
+} ooc_gemm_desc;
+
+#define OOC_BATCH_GRAPH 2u  /* capture the whole batched pipeline as one CUDA graph, then launch it */
+
+/*
+ * A stream of uneven out-of-core DGEMMs in one call (each one the Section IV
+ * problem on its own operands; problems must not share output memory).  The
+ * device budget is split into two halves: consecutive problems alternate
+ * halves and compute streams, so the copies and kernels of problem g + 1
+ * overlap problem g, while problem g + 2 waits for problem g to finish.  Each
+ * problem is planned for half the budget with opts (form: FP64 or Ozaki).
+ * With OOC_BATCH_GRAPH in opts->flags the issued copies, kernels and events
+ * are captured into one CUDA graph and launched as a single graph.  stats
+ * (nullable) receives totals: seconds, device_seconds, kernel_seconds (0 in
+ * graph mode, where launches inside the graph are not timed), tflops (sum of
+ * 2MNK over the call's wall time), bytes, blocks, steps, kernel_launches and
+ * the arena size in device_bytes.  Synchronous.
+ */
+int ooc_dgemm_batched(int32_t count, const ooc_gemm_desc* descs, size_t device_budget_bytes,
+                      const ooc_opts* opts, ooc_stats* stats);
+
 /*
  * In-core device GEMM (the paper's runtime DGEMM call of the pipeline's
  * compute stage): C = alpha * op(A) * op(B) + beta * C on device pointers,

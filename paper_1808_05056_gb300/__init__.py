@@ -58,7 +58,17 @@ class ooc_sched_op(ctypes.Structure):
                 ("read_tag", (ctypes.c_int64 * 4) * 3)]
 
 
-EXPORTS = ("ooc_dgemm", "ooc_sgemm", "ooc_dgemm_device", "ooc_plan", "ooc_schedule",
+class ooc_gemm_desc(ctypes.Structure):
+    _fields_ = [("transA", ctypes.c_char), ("transB", ctypes.c_char), ("reserved", ctypes.c_char * 6),
+                ("M", ctypes.c_int64), ("N", ctypes.c_int64), ("K", ctypes.c_int64),
+                ("alpha", ctypes.c_double), ("beta", ctypes.c_double),
+                ("A", ctypes.c_void_p), ("lda", ctypes.c_int64), ("B", ctypes.c_void_p), ("ldb", ctypes.c_int64),
+                ("C", ctypes.c_void_p), ("ldc", ctypes.c_int64)]
+
+
+OOC_BATCH_GRAPH = 2
+
+EXPORTS = ("ooc_dgemm", "ooc_sgemm", "ooc_dgemm_batched", "ooc_dgemm_device", "ooc_plan", "ooc_schedule",
            "ooc_query_device", "ooc_strerror", "ooc_last_error")
 
 _lib = None
@@ -160,6 +170,31 @@ def ooc_sgemm(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, budg
     return lib.ooc_sgemm(transA.encode(), transB.encode(), M, N, K, alpha, _ptr(A), lda, _ptr(B), ldb,
                          beta, _ptr(C), ldc, budget, ctypes.byref(opts) if opts is not None else None,
                          ctypes.byref(stats) if stats is not None else None)
+
+
+def ooc_dgemm_batched(descs, budget, opts=None, stats=None):
+    """C ABI ooc_dgemm_batched on a list of ooc_gemm_desc; returns the status code."""
+    lib = load()
+    f = lib.ooc_dgemm_batched
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_int32, ctypes.POINTER(ooc_gemm_desc), ctypes.c_size_t, ctypes.POINTER(ooc_opts),
+                  ctypes.POINTER(ooc_stats)]
+    arr = (ooc_gemm_desc * max(1, len(descs)))(*descs)
+    return f(len(descs), arr, budget, ctypes.byref(opts) if opts is not None else None,
+             ctypes.byref(stats) if stats is not None else None)
+
+
+def gemm_desc(transA, transB, A, B, C, alpha=1.0, beta=0.0):
+    """An ooc_gemm_desc for pinned host tensors (shapes as in dgemm)."""
+    M, N, K = _shape_args(transA, transB, A, B, C)
+    d = ooc_gemm_desc()
+    d.transA, d.transB = transA.encode(), transB.encode()
+    d.M, d.N, d.K = M, N, K
+    d.alpha, d.beta = alpha, beta
+    d.A, d.lda = _ptr(A), _ld(A)
+    d.B, d.ldb = _ptr(B), _ld(B)
+    d.C, d.ldc = _ptr(C), _ld(C)
+    return d
 
 
 def ooc_dgemm_device(transA, transB, M, N, K, alpha, dA, lda, dB, ldb, beta, dC, ldc, stream=None):

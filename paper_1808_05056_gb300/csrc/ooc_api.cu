@@ -233,9 +233,16 @@ struct TraceRec {
 // Resources of one call, released in the destructor after the streams drain.
 struct Exec {
     Plan p;
-    char* arena = nullptr;
+    char* arena = nullptr;     // device arena; its first word is the launch error word
+    char* base = nullptr;      // base of the current plan's slot region inside the arena
     bool own_arena = false;
     cudaStream_t st[3] = {nullptr, nullptr, nullptr};
+    cudaStream_t extra_compute = nullptr;  // second compute stream (batched calls)
+    cudaStream_t smap[3] = {nullptr, nullptr, nullptr};  // schedule stream id -> stream for the current plan
+    int ev_base = 0;           // offset of the current plan's events in ev
+    bool time_kernels = true;  // record timing events around tile launches (not inside graph capture)
+    double h2d = 0, d2h = 0;
+    long n_copy = 0, n_kern = 0;
     std::vector<cudaEvent_t> ev;
     std::vector<cudaEvent_t> kev;  // timing pairs around tile kernels
     std::vector<TraceRec> trace;
@@ -259,7 +266,10 @@ struct Exec {
         if (t_begin) cudaEventDestroy(t_begin);
         t_begin = nullptr;
         for (auto& e : t_end) { if (e) cudaEventDestroy(e); e = nullptr; }
+        if (extra_compute) cudaStreamSynchronize(extra_compute);
         for (auto& s : st) { if (s) cudaStreamDestroy(s); s = nullptr; }
+        if (extra_compute) cudaStreamDestroy(extra_compute);
+        extra_compute = nullptr;
         if (own_arena && arena) cudaFree(arena);
         arena = nullptr;
         own_arena = false;
@@ -284,7 +294,7 @@ int launch_split_tile(const Plan& p, const Op& op, Exec& x, const Operands& o, i
     const int64_t k_pad = split_k_pad(p);
     const int64_t ra_pad = split_rows_pad(p.mb), rb_pad = split_rows_pad(p.nb);
     int* err = reinterpret_cast<int*>(x.arena);
-    void* st = x.st[kStreamCompute];
+    void* st = x.smap[kStreamCompute];
     struct Side {
         int slot;
         bool is_a;
@@ -294,7 +304,7 @@ int launch_split_tile(const Plan& p, const Op& op, Exec& x, const Operands& o, i
     for (int q = 0; q < 2; ++q) {
         const int s = sides[q].slot;
         if (s < 0) continue;
-        char* aux = x.arena + slot_aux_offset(p, s);
+        char* aux = x.base + slot_aux_offset(p, s);
         const int64_t rpad = sides[q].is_a ? ra_pad : rb_pad;
         planes[q] = aux;
         exps[q] = reinterpret_cast<int*>(aux + split_planes_bytes(p, sides[q].is_a ? p.mb : p.nb));
@@ -304,7 +314,7 @@ int launch_split_tile(const Plan& p, const Op& op, Exec& x, const Operands& o, i
         const bool kmajor = sides[q].is_a ? !p.ta : p.tb;
         const int64_t ld = sides[q].is_a ? p.lda_dev : p.ldb_dev;
         const int64_t sr = kmajor ? ld : 1, sk = kmajor ? 1 : ld;
-        const char* src = x.arena + slot_offset(p, s);
+        const char* src = x.base + slot_offset(p, s);
         int rc;
         x.launches += ozaki ? (K > 0 ? 3 : 2) : 1;
         if (ozaki) {
@@ -356,7 +366,7 @@ int launch_split_tile(const Plan& p, const Op& op, Exec& x, const Operands& o, i
     P.beta = op.first ? o.beta : 1.0;
     P.read_c = !op.first || o.beta != 0.0;
     P.c_fp32 = p.es == 4;
-    P.C = x.arena + slot_offset(p, sc);
+    P.C = x.base + slot_offset(p, sc);
     P.ldc = p.ldc_dev;
     P.err = err;
     P.kblock = 64;
@@ -377,15 +387,103 @@ int launch_tile(const Plan& p, const Op& op, Exec& x, const Operands& o, std::st
     int* err = reinterpret_cast<int*>(x.arena);
     if (p.form == OOC_FORM_BF16X3 || p.form == OOC_FORM_OZAKI) return launch_split_tile(p, op, x, o, sa, sb, sc, why);
     if (p.form == OOC_FORM_FP64) {
-        const double* dA = sa >= 0 ? reinterpret_cast<const double*>(x.arena + slot_offset(p, sa)) : nullptr;
-        const double* dB = sb >= 0 ? reinterpret_cast<const double*>(x.arena + slot_offset(p, sb)) : nullptr;
-        double* dC = reinterpret_cast<double*>(x.arena + slot_offset(p, sc));
+        const double* dA = sa >= 0 ? reinterpret_cast<const double*>(x.base + slot_offset(p, sa)) : nullptr;
+        const double* dB = sb >= 0 ? reinterpret_cast<const double*>(x.base + slot_offset(p, sb)) : nullptr;
+        double* dC = reinterpret_cast<double*>(x.base + slot_offset(p, sc));
         ++x.launches;
         return launch_fp64_tile(!p.ta, p.tb, rows, cols, kk, o.alpha, dA, p.lda_dev, dB, p.ldb_dev, beta_eff, read_c,
-                                dC, p.ldc_dev, err, x.st[kStreamCompute], why);
+                                dC, p.ldc_dev, err, x.smap[kStreamCompute], why);
     }
     why = "contraction form not available in this build";
     return OOC_ERR_UNSUPPORTED;
+}
+
+// Issue one plan's schedule: copies, tile launches and the events ordering
+// them, on the streams x.smap, with the plan's slots at x.base and its events
+// at x.ev[x.ev_base + id].
+int issue_ops(Exec& x, const Plan& p, const std::vector<Op>& ops, const Operands& o, int es, const Inject& inj,
+              std::string& why)
+{
+    int rc = 0;
+    const char* hA = static_cast<const char*>(o.A);
+    const char* hB = static_cast<const char*>(o.B);
+    char* hC = static_cast<char*>(o.C);
+    const char* trace_path = std::getenv("OOC_TRACE");
+    const auto t_issue0 = std::chrono::steady_clock::now();
+    for (const Op& op : ops) {
+        cudaStream_t s = x.smap[op.stream];
+        const bool traced = trace_path && (op.kind == kH2D || op.kind == kKernel || op.kind == kD2H);
+        if (traced) {
+            TraceRec r{op.kind, op.stream, op.i, op.j, op.kc, 0.0,
+                       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_issue0).count(),
+                       nullptr, nullptr};
+            CK(cudaEventCreate(&r.e0));
+            CK(cudaEventCreate(&r.e1));
+            CK(cudaEventRecord(r.e0, s));
+            x.trace.push_back(r);
+        }
+        switch (op.kind) {
+        case kRecord: CK(cudaEventRecord(x.ev[x.ev_base + op.event], s)); break;
+        case kWait: CK(cudaStreamWaitEvent(s, x.ev[x.ev_base + op.event], 0)); break;
+        case kH2D: {
+            if (inj.copy >= 0 && x.n_copy++ == inj.copy) return fail(OOC_ERR_INJECTED, "injected copy failure");
+            const Tag& t = op.wtag;
+            char* dst = x.base + slot_offset(p, op.wslot);
+            ++x.gen[op.wslot];
+            const char* src;
+            int64_t rows, width, spitch, dpitch;
+            if (t.m == kMatA) {
+                const int64_t r0 = t.r * p.mb, k0 = t.c * p.kb, mr = p.rows_of(t.r), kr = p.k_of(t.c);
+                if (!p.ta) { src = hA + (r0 * o.lda + k0) * es; rows = mr; width = kr; }
+                else { src = hA + (k0 * o.lda + r0) * es; rows = kr; width = mr; }
+                spitch = o.lda * es; dpitch = p.lda_dev * es;
+            } else if (t.m == kMatB) {
+                const int64_t k0 = t.r * p.kb, c0 = t.c * p.nb, kr = p.k_of(t.r), nc = p.cols_of(t.c);
+                if (!p.tb) { src = hB + (k0 * o.ldb + c0) * es; rows = kr; width = nc; }
+                else { src = hB + (c0 * o.ldb + k0) * es; rows = nc; width = kr; }
+                spitch = o.ldb * es; dpitch = p.ldb_dev * es;
+            } else {
+                src = hC + (t.r * p.mb * o.ldc + t.c * p.nb) * es;
+                rows = p.rows_of(t.r); width = p.cols_of(t.c);
+                spitch = o.ldc * es; dpitch = p.ldc_dev * es;
+            }
+            if (rows > 0 && width > 0) {
+                if (spitch == width * es && dpitch == width * es)
+                    CK(cudaMemcpyAsync(dst, src, rows * width * es, cudaMemcpyHostToDevice, s));
+                else
+                    CK(cudaMemcpy2DAsync(dst, dpitch, src, spitch, width * es, rows, cudaMemcpyHostToDevice, s));
+                x.h2d += (double)rows * width * es;
+            }
+            break;
+        }
+        case kKernel: {
+            if (inj.kernel >= 0 && x.n_kern == inj.kernel) return fail(OOC_ERR_INJECTED, "injected kernel failure");
+            if (x.time_kernels) CK(cudaEventRecord(x.kev[2 * x.n_kern], s));
+            rc = launch_tile(p, op, x, o, why);
+            if (rc) return fail(rc, why);
+            if (x.time_kernels) CK(cudaEventRecord(x.kev[2 * x.n_kern + 1], s));
+            ++x.n_kern;
+            break;
+        }
+        case kD2H: {
+            const int64_t rows = p.rows_of(op.i), width = p.cols_of(op.j);
+            char* dst = hC + (op.i * p.mb * o.ldc + op.j * p.nb) * es;
+            const char* src = x.base + slot_offset(p, op.rslot[0]);
+            if (o.ldc == width && p.ldc_dev == width)
+                CK(cudaMemcpyAsync(dst, src, rows * width * es, cudaMemcpyDeviceToHost, s));
+            else
+                CK(cudaMemcpy2DAsync(dst, o.ldc * es, src, p.ldc_dev * es, width * es, rows, cudaMemcpyDeviceToHost,
+                                     s));
+            x.d2h += (double)rows * width * es;
+            break;
+        }
+        }
+        if (traced) {
+            CK(cudaEventRecord(x.trace.back().e1, s));
+            x.trace.back().bytes = x.h2d + x.d2h;  // running total; differenced when written
+        }
+    }
+    return OOC_OK;
 }
 
 int run_ooc(char ta, char tb, int64_t M, int64_t N, int64_t K, const Operands& o, int es, size_t budget,
@@ -452,86 +550,12 @@ int run_ooc(char ta, char tb, int64_t M, int64_t N, int64_t K, const Operands& o
     CK(cudaStreamWaitEvent(x.st[kStreamD2H], x.t_begin, 0));
     CK(cudaMemsetAsync(err, 0, sizeof(int), x.st[kStreamCompute]));
 
-    long n_copy = 0, n_kern = 0;
-    double h2d = 0, d2h = 0;
-    const char* hA = static_cast<const char*>(o.A);
-    const char* hB = static_cast<const char*>(o.B);
-    char* hC = static_cast<char*>(o.C);
+    x.base = x.arena;
+    x.smap[0] = x.st[0]; x.smap[1] = x.st[1]; x.smap[2] = x.st[2];
+    x.ev_base = 0;
+    rc = issue_ops(x, p, ops, o, es, inj, why);
+    if (rc) return rc;
     const char* trace_path = std::getenv("OOC_TRACE");
-    const auto t_issue0 = std::chrono::steady_clock::now();
-    for (const Op& op : ops) {
-        cudaStream_t s = x.st[op.stream];
-        const bool traced = trace_path && (op.kind == kH2D || op.kind == kKernel || op.kind == kD2H);
-        if (traced) {
-            TraceRec r{op.kind, op.stream, op.i, op.j, op.kc, 0.0,
-                       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_issue0).count(),
-                       nullptr, nullptr};
-            CK(cudaEventCreate(&r.e0));
-            CK(cudaEventCreate(&r.e1));
-            CK(cudaEventRecord(r.e0, s));
-            x.trace.push_back(r);
-        }
-        switch (op.kind) {
-        case kRecord: CK(cudaEventRecord(x.ev[op.event], s)); break;
-        case kWait: CK(cudaStreamWaitEvent(s, x.ev[op.event], 0)); break;
-        case kH2D: {
-            if (inj.copy >= 0 && n_copy++ == inj.copy) return fail(OOC_ERR_INJECTED, "injected copy failure");
-            const Tag& t = op.wtag;
-            char* dst = x.arena + slot_offset(p, op.wslot);
-            ++x.gen[op.wslot];
-            const char* src;
-            int64_t rows, width, spitch, dpitch;
-            if (t.m == kMatA) {
-                const int64_t r0 = t.r * p.mb, k0 = t.c * p.kb, mr = p.rows_of(t.r), kr = p.k_of(t.c);
-                if (!p.ta) { src = hA + (r0 * o.lda + k0) * es; rows = mr; width = kr; }
-                else { src = hA + (k0 * o.lda + r0) * es; rows = kr; width = mr; }
-                spitch = o.lda * es; dpitch = p.lda_dev * es;
-            } else if (t.m == kMatB) {
-                const int64_t k0 = t.r * p.kb, c0 = t.c * p.nb, kr = p.k_of(t.r), nc = p.cols_of(t.c);
-                if (!p.tb) { src = hB + (k0 * o.ldb + c0) * es; rows = kr; width = nc; }
-                else { src = hB + (c0 * o.ldb + k0) * es; rows = nc; width = kr; }
-                spitch = o.ldb * es; dpitch = p.ldb_dev * es;
-            } else {
-                src = hC + (t.r * p.mb * o.ldc + t.c * p.nb) * es;
-                rows = p.rows_of(t.r); width = p.cols_of(t.c);
-                spitch = o.ldc * es; dpitch = p.ldc_dev * es;
-            }
-            if (rows > 0 && width > 0) {
-                if (spitch == width * es && dpitch == width * es)
-                    CK(cudaMemcpyAsync(dst, src, rows * width * es, cudaMemcpyHostToDevice, s));
-                else
-                    CK(cudaMemcpy2DAsync(dst, dpitch, src, spitch, width * es, rows, cudaMemcpyHostToDevice, s));
-                h2d += (double)rows * width * es;
-            }
-            break;
-        }
-        case kKernel: {
-            if (inj.kernel >= 0 && n_kern == inj.kernel) return fail(OOC_ERR_INJECTED, "injected kernel failure");
-            CK(cudaEventRecord(x.kev[2 * n_kern], s));
-            rc = launch_tile(p, op, x, o, why);
-            if (rc) return fail(rc, why);
-            CK(cudaEventRecord(x.kev[2 * n_kern + 1], s));
-            ++n_kern;
-            break;
-        }
-        case kD2H: {
-            const int64_t rows = p.rows_of(op.i), width = p.cols_of(op.j);
-            char* dst = hC + (op.i * p.mb * o.ldc + op.j * p.nb) * es;
-            const char* src = x.arena + slot_offset(p, op.rslot[0]);
-            if (o.ldc == width && p.ldc_dev == width)
-                CK(cudaMemcpyAsync(dst, src, rows * width * es, cudaMemcpyDeviceToHost, s));
-            else
-                CK(cudaMemcpy2DAsync(dst, o.ldc * es, src, p.ldc_dev * es, width * es, rows, cudaMemcpyDeviceToHost,
-                                     s));
-            d2h += (double)rows * width * es;
-            break;
-        }
-        }
-        if (traced) {
-            CK(cudaEventRecord(x.trace.back().e1, s));
-            x.trace.back().bytes = h2d + d2h;  // running total; differenced when written
-        }
-    }
     for (int i = 0; i < 3; ++i) CK(cudaEventRecord(x.t_end[i], x.st[i]));
     for (auto s : x.st) CK(cudaStreamSynchronize(s));
     int herr = 0;
@@ -563,14 +587,14 @@ int run_ooc(char ta, char tb, int64_t M, int64_t N, int64_t K, const Operands& o
             best = std::max(best, ms);
         }
         double ksum = 0;
-        for (int64_t k = 0; k < n_kern; ++k) {
+        for (int64_t k = 0; k < x.n_kern; ++k) {
             CK(cudaEventElapsedTime(&ms, x.kev[2 * k], x.kev[2 * k + 1]));
             ksum += ms;
         }
         stats->device_seconds = best * 1e-3;
         stats->kernel_seconds = ksum * 1e-3;
-        stats->h2d_bytes = h2d;
-        stats->d2h_bytes = d2h;
+        stats->h2d_bytes = x.h2d;
+        stats->d2h_bytes = x.d2h;
         stats->mb = p.mb; stats->nb = p.nb; stats->kb = p.kb;
         stats->depth = p.nA; stats->c_buffers = p.nC; stats->b_buffers = p.nB; stats->form = p.form;
         stats->blocks = p.h * p.w; stats->steps = p.h * p.w * p.nkc;
@@ -587,9 +611,194 @@ int run_ooc(char ta, char tb, int64_t M, int64_t N, int64_t K, const Operands& o
     return OOC_OK;
 }
 
+int run_batched(int32_t count, const ooc_gemm_desc* d, size_t budget, const ooc_opts* opts_in, ooc_stats* stats)
+{
+    const auto t_host0 = std::chrono::steady_clock::now();
+    std::string why;
+    if (count < 0 || (count > 0 && !d)) return fail(OOC_ERR_INVALID_ARG, "batched: bad count or descriptor array");
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    int rc;
+    for (int g = 0; g < count; ++g) {
+        rc = validate(d[g].transA, d[g].transB, d[g].M, d[g].N, d[g].K, d[g].A, d[g].lda, d[g].B, d[g].ldb, d[g].C,
+                      d[g].ldc, d[g].beta != 0.0, why);
+        if (rc) return fail(rc, "batched problem " + std::to_string(g) + ": " + why);
+    }
+    if (count == 0) return OOC_OK;
+    rc = check_device(why);
+    if (rc) return fail(rc, why);
+    for (int g = 0; g < count; ++g) {
+        if (d[g].M == 0 || d[g].N == 0) continue;
+        const bool ta = is_t(d[g].transA), tb = is_t(d[g].transB);
+        if (!range_pinned(d[g].A, ta ? d[g].K : d[g].M, ta ? d[g].M : d[g].K, d[g].lda, 8) ||
+            !range_pinned(d[g].B, tb ? d[g].N : d[g].K, tb ? d[g].K : d[g].N, d[g].ldb, 8) ||
+            !range_pinned(d[g].C, d[g].M, d[g].N, d[g].ldc, 8))
+            return fail(OOC_ERR_NOT_PINNED, "batched problem " + std::to_string(g) + ": host operands must be page-locked");
+    }
+    ooc_opts opts;
+    std::memset(&opts, 0, sizeof(opts));
+    if (opts_in) opts = *opts_in;
+    const bool use_graph = (opts.flags & OOC_BATCH_GRAPH) != 0;
+    double hg = 0, dg = 0;
+    const bool have_link = ooc_query_device(nullptr, &hg, &dg) == OOC_OK && hg > 0 && dg > 0;
+    const size_t half = ((budget > 512 ? budget - 256 : 0) / 2) / 256 * 256;
+
+    // plans and schedules, each within half of the budget
+    std::vector<Plan> plans(count);
+    std::vector<std::vector<Op>> sched(count);
+    int E = 0;
+    int64_t nkern = 0;
+    double flops = 0;
+    for (int g = 0; g < count; ++g) {
+        if (d[g].M == 0 || d[g].N == 0) continue;
+        PlanRequest rq{d[g].M, d[g].N, d[g].K, 8, d[g].beta != 0.0, is_t(d[g].transA), is_t(d[g].transB), half, opts};
+        rq.lda = d[g].lda; rq.ldb = d[g].ldb; rq.ldc = d[g].ldc;
+        if (have_link) { rq.h2d_gbps = hg; rq.d2h_gbps = dg; }
+        rc = make_plan(rq, plans[g], why);
+        if (rc) return fail(rc, "batched problem " + std::to_string(g) + ": " + why);
+        build_schedule(plans[g], sched[g]);
+        E = std::max(E, n_events(plans[g]));
+        for (const Op& op : sched[g]) nkern += op.kind == kKernel;
+        flops += 2.0 * (double)d[g].M * d[g].N * d[g].K;
+    }
+
+    Inject inj;
+    Exec x;
+    if (opts.workspace) {
+        if (opts.workspace_bytes < 2 * half + 256) return fail(OOC_ERR_INVALID_ARG, "workspace smaller than the budget");
+        x.arena = static_cast<char*>(opts.workspace);
+    } else {
+        if (inj.alloc) return fail(OOC_ERR_INJECTED, "injected arena allocation failure");
+        if (cudaMalloc(&x.arena, 2 * half + 256) != cudaSuccess) {
+            cudaGetLastError();
+            x.arena = nullptr;
+            return fail(OOC_ERR_ALLOC, "device arena of " + std::to_string(2 * half + 256) + " bytes");
+        }
+        x.own_arena = true;
+    }
+    for (auto& st : x.st) CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&x.extra_compute, cudaStreamNonBlocking));
+    x.ev.resize(2 * E + 2 + 4, nullptr);  // two event sets, two "half done" events, fork/join
+    for (auto& e : x.ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    x.kev.resize(2 * nkern, nullptr);
+    for (auto& e : x.kev) CK(cudaEventCreate(&e));
+    CK(cudaEventCreate(&x.t_begin));
+    for (auto& e : x.t_end) CK(cudaEventCreate(&e));
+    const int ev_done0 = 2 * E, ev_fork = 2 * E + 2;
+
+    cudaStream_t s0 = x.st[kStreamH2D];
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    // Timing events cannot be read back from inside a captured graph: in graph
+    // mode the launch is timed from outside and tile launches are not timed.
+    x.time_kernels = !use_graph;
+    if (use_graph) CK(cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal));
+    else CK(cudaEventRecord(x.t_begin, s0));
+    CK(cudaEventRecord(x.ev[ev_fork], s0));
+    CK(cudaStreamWaitEvent(x.st[kStreamCompute], x.ev[ev_fork], 0));
+    CK(cudaStreamWaitEvent(x.st[kStreamD2H], x.ev[ev_fork], 0));
+    CK(cudaStreamWaitEvent(x.extra_compute, x.ev[ev_fork], 0));
+    CK(cudaMemsetAsync(x.arena, 0, sizeof(int), s0));
+    bool issued_half[2] = {false, false};
+    for (int g = 0; g < count; ++g) {
+        if (d[g].M == 0 || d[g].N == 0) continue;
+        const int h = g & 1;
+        x.base = x.arena + 256 + (size_t)h * half;
+        x.smap[kStreamH2D] = x.st[kStreamH2D];
+        x.smap[kStreamCompute] = h ? x.extra_compute : x.st[kStreamCompute];
+        x.smap[kStreamD2H] = x.st[kStreamD2H];
+        x.ev_base = h * E;
+        if (issued_half[h]) {
+            // the previous problem in this half has copied its last block out
+            CK(cudaStreamWaitEvent(x.smap[kStreamH2D], x.ev[ev_done0 + h], 0));
+            CK(cudaStreamWaitEvent(x.smap[kStreamCompute], x.ev[ev_done0 + h], 0));
+        }
+        x.gen.assign(plans[g].slots(), 0);
+        x.split_gen.assign(plans[g].slots(), -1);
+        Operands o{d[g].A, d[g].lda, d[g].B, d[g].ldb, d[g].C, d[g].ldc, d[g].alpha, d[g].beta};
+        rc = issue_ops(x, plans[g], sched[g], o, 8, inj, why);
+        if (rc) {
+            if (use_graph) {
+                cudaGraph_t gg = nullptr;
+                cudaStreamEndCapture(s0, &gg);
+                if (gg) cudaGraphDestroy(gg);
+                cudaGetLastError();
+            }
+            return rc;
+        }
+        CK(cudaEventRecord(x.ev[ev_done0 + h], x.st[kStreamD2H]));
+        issued_half[h] = true;
+    }
+    CK(cudaEventRecord(x.ev[ev_fork + 1], x.st[kStreamCompute]));
+    CK(cudaEventRecord(x.ev[ev_fork + 2], x.st[kStreamD2H]));
+    CK(cudaEventRecord(x.ev[ev_fork + 3], x.extra_compute));
+    for (int k = 1; k <= 3; ++k) CK(cudaStreamWaitEvent(s0, x.ev[ev_fork + k], 0));
+    if (!use_graph) {
+        for (auto& e : x.t_end) CK(cudaEventRecord(e, s0));
+    } else {
+        CK(cudaStreamEndCapture(s0, &graph));
+        cudaError_t e = cudaGraphInstantiate(&gexec, graph, 0);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(graph);
+            return fail(OOC_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+        }
+        CK(cudaEventRecord(x.t_begin, s0));
+        e = cudaGraphLaunch(gexec, s0);
+        if (e != cudaSuccess) {
+            cudaGraphExecDestroy(gexec);
+            cudaGraphDestroy(graph);
+            return fail(OOC_ERR_CUDA, std::string("cudaGraphLaunch: ") + cudaGetErrorString(e));
+        }
+        for (auto& ev : x.t_end) CK(cudaEventRecord(ev, s0));
+    }
+    cudaError_t se = cudaStreamSynchronize(s0);
+    for (auto st : x.st) cudaStreamSynchronize(st);
+    cudaStreamSynchronize(x.extra_compute);
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (graph) cudaGraphDestroy(graph);
+    if (se != cudaSuccess) return fail(OOC_ERR_CUDA, std::string("batched pipeline: ") + cudaGetErrorString(se));
+    int herr = 0;
+    CK(cudaMemcpy(&herr, x.arena, sizeof(int), cudaMemcpyDeviceToHost));
+    if (herr != 0) return fail(OOC_ERR_TIMEOUT, "a device-side wait gave up (status " + std::to_string(herr) + ")");
+    if (stats) {
+        float ms = 0, best = 0;
+        for (auto e : x.t_end) {
+            CK(cudaEventElapsedTime(&ms, x.t_begin, e));
+            best = std::max(best, ms);
+        }
+        double ksum = 0;
+        for (int64_t k = 0; x.time_kernels && k < x.n_kern; ++k) {
+            CK(cudaEventElapsedTime(&ms, x.kev[2 * k], x.kev[2 * k + 1]));
+            ksum += ms;
+        }
+        stats->device_seconds = best * 1e-3;
+        stats->kernel_seconds = ksum * 1e-3;  // 0 in graph mode (not timed)
+        stats->h2d_bytes = x.h2d;
+        stats->d2h_bytes = x.d2h;
+        for (int g = 0; g < count; ++g) {
+            stats->blocks += plans[g].h * plans[g].w;
+            stats->steps += plans[g].h * plans[g].w * plans[g].nkc;
+        }
+        stats->device_bytes = (int64_t)(2 * half + 256);
+        stats->form = opts.form ? opts.form : OOC_FORM_FP64;
+        stats->kernel_launches = x.launches;
+    }
+    x.release();
+    if (stats) {
+        stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_host0).count();
+        stats->tflops = stats->seconds > 0 ? flops / stats->seconds / 1e12 : 0.0;
+    }
+    return OOC_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+int ooc_dgemm_batched(int32_t count, const ooc_gemm_desc* descs, size_t device_budget_bytes, const ooc_opts* opts,
+                      ooc_stats* stats)
+{
+    return run_batched(count, descs, device_budget_bytes, opts, stats);
+}
 
 const char* ooc_strerror(int code)
 {
