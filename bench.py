@@ -41,10 +41,27 @@ CONFIGS = {
     "fp64-1024": ("fp64", 1024, 1024, 1024, 1.0, 0.0, 4 << 20, synth.UNIFORM),
     "ozaki-65536": ("ozaki", 65536, 65536, 16384, 1.0, 0.0, 16 << 30, synth.LOGSPREAD),
     "bf16x3-65536": ("bf16x3", 65536, 65536, 65536, 1.0, 1.0, 8 << 30, synth.UNIFORM),
+    # 256 uneven FP64 problems, M, N, K log-uniform in [512, 32768], ~64 GiB host in total
+    "batched-256": ("batched", 256, 512, 32768, 1.0, 0.0, 8 << 30, synth.NORMAL),
 }
 # per form: (element dtype name, relative Frobenius tolerance, products per logical product, dtype tag)
 FORMS = {"fp64": ("float64", 1e-13, 1, "f64"), "ozaki": ("float64", 1e-12, 36, "f64 (bf16 digit planes)"),
-         "bf16x3": ("float32", 1e-6, 6, "f32 (bf16x3 pieces)")}
+         "bf16x3": ("float32", 1e-6, 6, "f32 (bf16x3 pieces)"), "batched": ("float64", 1e-13, 1, "f64")}
+
+
+def batch_shapes(seed, count, lo, hi, cap=64 << 30, es=8):
+    """Seeded (M, N, K) triples, each dimension log-uniform in [lo, hi]; a draw is
+    kept only while the running host footprint stays within its pro-rata share
+    of `cap` (count problems in about `cap` bytes of host memory)."""
+    rng = np.random.default_rng(seed)
+    out, used = [], 0
+    while len(out) < count:
+        m, n, k = (int(round(np.exp(rng.uniform(np.log(lo), np.log(hi))))) for _ in range(3))
+        fp = (m * k + k * n + m * n) * es
+        if used + fp <= cap * (len(out) + 1) / count:
+            out.append((m, n, k))
+            used += fp
+    return out
 NOMINAL_FP64_TF, NOMINAL_BF16_TF = 1.25, 2250.0
 
 
@@ -64,7 +81,7 @@ def parse():
 
 def workload(args):
     form, M, N, K, alpha, beta, budget, dist = CONFIGS[args.config]
-    if args.n:
+    if args.n and form != "batched":
         K = max(1, K * args.n // M)
         M = N = args.n
     if args.budget_gib:
@@ -365,12 +382,148 @@ def run_ours(args, w, world, rank, local, pg):
     print(json.dumps(line), flush=True)
 
 
+def run_batched_bench(args, w, world, rank, local, pg):
+    """Batched configuration: one ooc_dgemm_batched call over all problems per step
+    (--impl reference: the oracle on sampled blocks of the same problems)."""
+    import torch
+    count, lo, hi = w["M"], w["N"], w["K"]
+    if args.n:  # smaller runs: fewer, smaller problems
+        count, hi = max(4, args.n // 128), max(lo, min(hi, args.n))
+    shapes = batch_shapes(1234, count, lo, hi)
+    flops = sum(2.0 * m * n * k for m, n, k in shapes)
+    r = 32
+    cores = host_cores()
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        picks = list(range(0, len(shapes), max(1, len(shapes) // 8)))[:8]
+        per = []
+        for q in picks:
+            m, n, k = shapes[q]
+            A = torch.empty((m, k), dtype=torch.float64); B = torch.empty((k, n), dtype=torch.float64)
+            synth.fill(A, 100 + q, 0, w["dist"]); synth.fill(B, 100 + q, 1, w["dist"])
+            per.append((q, A, B))
+        times = []
+        for it in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            for q, A, B in per:
+                m, n, k = shapes[q]
+                wq = dict(w, M=m, N=n, K=k, beta=0.0)
+                oracle_sample(wq, A, B, [None], sample_blocks(wq, 1, r, seed=q), r, cores)
+            if it >= args.warmup:
+                times.append(time.perf_counter() - t0)
+        fl = sum(2.0 * r * r * shapes[q][2] for q, _, _ in per)
+        value = fl * len(times) / sum(times) / 1e12
+        line = {"impl": "reference", "metric": "out-of-core GEMM effective TFLOP/s incl. transfers", "value": value,
+                "unit": "TFLOP/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Philox)",
+                "config": {"workload": "%d uneven FP64 GEMMs, M,N,K log-uniform [%d, %d]" % (len(shapes), lo, hi)},
+                "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                                 "sample": "one %dx%d block of C in each of %d of the problems per step" % (r, r, len(per))},
+                "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    import paper_1808_05056_gb300 as P
+    torch.cuda.set_device(local)
+    P.load()
+    ops = []
+    t_fill = time.perf_counter()
+    for q, (m, n, k) in enumerate(shapes):
+        A = torch.empty((m, k), dtype=torch.float64, pin_memory=True)
+        B = torch.empty((k, n), dtype=torch.float64, pin_memory=True)
+        C = torch.empty((m, n), dtype=torch.float64, pin_memory=True)
+        synth.fill(A, 100 + q + 1000 * rank, 0, w["dist"])
+        synth.fill(B, 100 + q + 1000 * rank, 1, w["dist"])
+        ops.append((A, B, C))
+    t_fill = time.perf_counter() - t_fill
+    descs = [P.gemm_desc("N", "N", A, B, C, w["alpha"], w["beta"]) for A, B, C in ops]
+    graph = os.environ.get("OOC_BENCH_GRAPH", "0") == "1"
+    opts = P.make_opts(form=P.OOC_FORM_FP64, flags=P.OOC_BATCH_GRAPH if graph else 0)
+
+    def step():
+        st = P.ooc_stats()
+        t0 = time.perf_counter()
+        rc = P.ooc_dgemm_batched(descs, w["budget"], opts, st)
+        wall = time.perf_counter() - t0
+        if rc != 0:
+            raise RuntimeError("ooc_dgemm_batched: %s: %s" % (P.ooc_strerror(rc), P.ooc_last_error()))
+        return st, wall
+
+    for _ in range(args.warmup):
+        step()
+    # parity on one sampled block of a spread of problems (beta = 0: C is recomputed each step)
+    parity = None
+    cpu = None
+    if rank == 0:
+        errs, t_or, fl = [], 0.0, 0.0
+        for q in range(0, len(shapes), max(1, len(shapes) // 8)):
+            m, n, k = shapes[q]
+            A, B, C = ops[q]
+            wq = dict(w, M=m, N=n, K=k)
+            blk = sample_blocks(wq, 1, r, seed=q)
+            ref, dt, used = oracle_sample(wq, A, B, [None], blk, r, cores)
+            t_or += dt
+            fl += 2.0 * r * r * k
+            i, j = blk[0]
+            got = C[i:i + r, j:j + r].numpy()
+            errs.append(float(np.linalg.norm(got - ref[0]) / np.linalg.norm(ref[0])))
+        parity = {"max_rel_fro": max(errs), "tolerance": 1e-13, "problems_checked": len(errs), "block": r,
+                  "pass": max(errs) <= 1e-13}
+        cpu = {"value": fl / t_or / 1e12, "unit": "TFLOP/s", "cores": used, "kind": "oracle",
+               "sample": "one %dx%d block of C in each of %d problems, %.1f s" % (r, r, len(errs), t_or)}
+    clk = ClockSampler(local, enabled=not args.no_clocks)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    stats = [step() for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    clocks = clk.stop()
+    dev_s = sum(st.device_seconds for st, _ in stats)
+    wall_s = sum(wl for _, wl in stats)
+    ker_s = sum(st.kernel_seconds for st, _ in stats)
+    if rank != 0:
+        return
+    s0 = stats[0][0]
+    pk, pk_src = peaks()
+    peak = pk["bf16_tflops_sustained"] * NOMINAL_FP64_TF / NOMINAL_BF16_TF
+    achieved = flops * args.steps / ker_s / 1e12 if ker_s > 0 else None
+    line = {
+        "metric": "out-of-core GEMM effective TFLOP/s incl. transfers",
+        "value": world * flops * args.steps / dev_s / 1e12, "unit": "TFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dev_s / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded Philox N(0,1), pinned host)",
+        "config": {"workload": "%d uneven FP64 GEMMs, M,N,K log-uniform in [%d, %d] (seed 1234), %.1f GiB host, "
+                               "device budget %.2f GiB, one ooc_dgemm_batched call per step%s" % (
+                                   len(shapes), lo, hi,
+                                   sum((m * k + k * n + m * n) * 8 for m, n, k in shapes) / 2 ** 30,
+                                   w["budget"] / 2 ** 30, " (CUDA graph)" if graph else ""),
+                   "problems": len(shapes), "total_flop": flops,
+                   "l2": "inputs larger than L2 (tens of GiB of host operands per step)"},
+        "roofline": {"bound": "tensor", "kernel": "fp64_tile_kernel (FP64 mma.sync, TMA-fed)",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak if achieved else None, "traffic": None,
+                     "peak_source": "%s bf16 sustained x nominal FP64/BF16 ratio" % pk_src},
+        "e2e": {"value": world * flops * args.steps / wall_s / 1e12, "unit": "TFLOP/s",
+                "h2d_bytes_per_step": s0.h2d_bytes, "d2h_bytes_per_step": s0.d2h_bytes},
+        "gpu_launches": sum(st.kernel_launches for st, _ in stats),
+        "parity": parity, "cpu_baseline": cpu, "clocks": clocks, "setup_fill_s": t_fill,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     w = workload(args)
     world, rank, local, pg = dist_init(args)
     args.gpus = world if world > 1 else args.gpus
-    if args.impl == "reference":
+    if w["form"] == "batched":
+        run_batched_bench(args, w, world, rank, local, pg)
+    elif args.impl == "reference":
         run_reference(args, w, world, rank, pg)
     else:
         run_ours(args, w, world, rank, local, pg)
