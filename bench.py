@@ -440,7 +440,15 @@ def run_batched_bench(args, w, world, rank, local, pg):
     t_fill = time.perf_counter() - t_fill
     descs = [P.gemm_desc("N", "N", A, B, C, w["alpha"], w["beta"]) for A, B, C in ops]
     graph = os.environ.get("OOC_BENCH_GRAPH", "0") == "1"
-    opts = P.make_opts(form=P.OOC_FORM_FP64, flags=P.OOC_BATCH_GRAPH if graph else 0)
+    # plans from the learned cost model when its file is present (else the analytic planner)
+    from paper_1808_05056_gb300 import tune
+    planner = "analytic"
+    flags = P.OOC_BATCH_GRAPH if graph else 0
+    if os.environ.get("OOC_BENCH_PLANNER", "model") == "model" and os.path.exists(tune.DEFAULT_MODEL):
+        tune.install()
+        flags |= P.OOC_PLAN_MODEL
+        planner = "learned cost model (%s)" % os.path.basename(tune.DEFAULT_MODEL)
+    opts = P.make_opts(form=P.OOC_FORM_FP64, flags=flags)
 
     def step():
         st = P.ooc_stats()
@@ -502,7 +510,7 @@ def run_batched_bench(args, w, world, rank, local, pg):
                                    len(shapes), lo, hi,
                                    sum((m * k + k * n + m * n) * 8 for m, n, k in shapes) / 2 ** 30,
                                    w["budget"] / 2 ** 30, " (CUDA graph)" if graph else ""),
-                   "problems": len(shapes), "total_flop": flops,
+                   "problems": len(shapes), "total_flop": flops, "planner": planner,
                    "l2": "inputs larger than L2 (tens of GiB of host operands per step)"},
         "roofline": {"bound": "tensor", "kernel": "fp64_tile_kernel (FP64 mma.sync, TMA-fed)",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",

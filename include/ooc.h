@@ -64,11 +64,13 @@ extern "C" {
 
 /* ---- plan selection flags (ooc_opts.flags) --------------------------- */
 #define OOC_PLAN_PAPER 1u  /* Section IV partitioner: equal h x w split, 2A + 1B + 2C buffers */
+#define OOC_PLAN_MODEL 4u  /* choose among candidates with the installed cost model (ooc_costmodel_set) */
 
 /*
  * Options; a zero-initialised struct means "choose automatically".
  * mb, nb, kb: C block rows, C block columns and K-chunk length.
- * depth: A-slice buffers (2 or 3); c_buffers: C-block buffers.
+ * depth: A-slice buffers (2 or 3); c_buffers: C-block buffers; b_buffers:
+ * B-chunk buffers (a whole column of B chunks keeps B resident per column).
  * slices: Ozaki slice count (0 = chosen from the input exponent spread).
  * workspace/workspace_bytes: optional caller-owned device memory for the
  * buffers (see the conventions above).
@@ -80,7 +82,7 @@ typedef struct {
     int32_t slices;
     int64_t mb, nb, kb;
     uint32_t flags;
-    uint32_t reserved;
+    int32_t b_buffers;   /* B-slot ring size (0 = automatic)                       */
     void* workspace;
     size_t workspace_bytes;
 } ooc_opts;
@@ -226,6 +228,60 @@ typedef struct {
 int ooc_schedule(int64_t M, int64_t N, int64_t K, int32_t elem_bytes, int32_t beta_nonzero,
                  size_t device_budget_bytes, const ooc_opts* opts, ooc_sched_op* out,
                  int64_t capacity, int64_t* count);
+
+/* ---- plan search: candidates, autotuner, learned cost model ------------ */
+/* The paper has no plan search beyond its partitioner (Section IV); these
+ * calls pick block/chunk/ring sizes for this hardware. */
+#define OOC_MLP_INPUTS 16
+#define OOC_MLP_PARAMS 5313
+
+/* One candidate plan and its cost-model features (see ooc_plan_candidates). */
+typedef struct {
+    int64_t mb, nb, kb;
+    int32_t depth, b_buffers, c_buffers, reserved;
+    double est_seconds;                 /* the planner's analytic estimate      */
+    float features[OOC_MLP_INPUTS];     /* inputs of the cost model             */
+} ooc_plan_candidate;
+
+/*
+ * The best `capacity` distinct plans for a problem by the planner's analytic
+ * estimate (host only).  Problem arguments as in ooc_plan; opts->form picks
+ * the form.  *count receives the number written.
+ */
+int ooc_plan_candidates(int64_t M, int64_t N, int64_t K, int32_t elem_bytes, int32_t beta_nonzero,
+                        size_t device_budget_bytes, const ooc_opts* opts, ooc_plan_candidate* out,
+                        int32_t capacity, int32_t* count);
+
+/*
+ * Exhaustive autotuner: run the problem once with each of the best
+ * `max_candidates` candidate plans (after one untimed warm-up run) and report
+ * each candidate's device time in seconds_out (same order as out).  The
+ * problem's C is overwritten by every run, so tune on scratch operands of the
+ * right shape.  elem_bytes 8 runs ooc_dgemm (desc pointers are double*),
+ * 4 runs ooc_sgemm (desc pointers are float*); opts->form picks the form.
+ */
+int ooc_autotune(const ooc_gemm_desc* desc, int32_t elem_bytes, size_t device_budget_bytes,
+                 const ooc_opts* opts, int32_t max_candidates, ooc_plan_candidate* out,
+                 double* seconds_out, int32_t* count);
+
+/*
+ * Cost-model MLP (16 -> 64 -> 64 -> 1, ReLU), parameters packed W1[64][16],
+ * b1[64], W2[64][64], b2[64], W3[64], b3 (OOC_MLP_PARAMS floats), all host
+ * arrays, computed on the GPU.  Predicts log2(seconds) of a candidate.
+ *   ooc_mlp_forward:   y[i] = f(X[i]) for n rows of OOC_MLP_INPUTS features
+ *   ooc_mlp_loss_grad: loss = mean of 0.5 (f(X[i]) - t[i])^2 and its gradient
+ *   ooc_mlp_train:     Adam (lr, betas 0.9/0.999, L2 weight decay added to the
+ *                      gradient) over seeded shuffled mini-batches; params are
+ *                      updated in place; final_loss (nullable) = loss of the
+ *                      result over all samples
+ *   ooc_costmodel_set: install params for OOC_PLAN_MODEL (NULL clears)
+ */
+int ooc_mlp_forward(const float* params, const float* X, int64_t n, float* y);
+int ooc_mlp_loss_grad(const float* params, const float* X, const float* t, int64_t n, float* grad,
+                      float* loss);
+int ooc_mlp_train(float* params, const float* X, const float* t, int64_t n, int32_t epochs,
+                  int32_t batch, float lr, float weight_decay, uint64_t seed, float* final_loss);
+int ooc_costmodel_set(const float* params, int64_t n);
 
 /*
  * hclGetMemSize analogue (Section III runtime methods): free device memory,

@@ -33,7 +33,7 @@ OOC_PLAN_PAPER = 1
 class ooc_opts(ctypes.Structure):
     _fields_ = [("form", ctypes.c_int32), ("depth", ctypes.c_int32), ("c_buffers", ctypes.c_int32),
                 ("slices", ctypes.c_int32), ("mb", ctypes.c_int64), ("nb", ctypes.c_int64),
-                ("kb", ctypes.c_int64), ("flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("kb", ctypes.c_int64), ("flags", ctypes.c_uint32), ("b_buffers", ctypes.c_int32),
                 ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t)]
 
 
@@ -67,8 +67,20 @@ class ooc_gemm_desc(ctypes.Structure):
 
 
 OOC_BATCH_GRAPH = 2
+OOC_PLAN_MODEL = 4
+OOC_MLP_INPUTS = 16
+OOC_MLP_PARAMS = 5313
+
+
+class ooc_plan_candidate(ctypes.Structure):
+    _fields_ = [("mb", ctypes.c_int64), ("nb", ctypes.c_int64), ("kb", ctypes.c_int64),
+                ("depth", ctypes.c_int32), ("b_buffers", ctypes.c_int32), ("c_buffers", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("est_seconds", ctypes.c_double),
+                ("features", ctypes.c_float * OOC_MLP_INPUTS)]
 
 EXPORTS = ("ooc_dgemm", "ooc_sgemm", "ooc_dgemm_batched", "ooc_dgemm_device", "ooc_plan", "ooc_schedule",
+           "ooc_plan_candidates", "ooc_autotune", "ooc_mlp_forward", "ooc_mlp_loss_grad", "ooc_mlp_train",
+           "ooc_costmodel_set",
            "ooc_query_device", "ooc_strerror", "ooc_last_error")
 
 _lib = None
@@ -119,10 +131,11 @@ def load(path=None):
 
 
 def _opts(form=0, depth=0, c_buffers=0, slices=0, mb=0, nb=0, kb=0, flags=0, workspace=None,
-          workspace_bytes=0):
+          workspace_bytes=0, b_buffers=0):
     o = ooc_opts()
     o.form, o.depth, o.c_buffers, o.slices = form, depth, c_buffers, slices
     o.mb, o.nb, o.kb, o.flags = mb, nb, kb, flags
+    o.b_buffers = b_buffers
     o.workspace = workspace
     o.workspace_bytes = workspace_bytes
     return o
@@ -247,6 +260,107 @@ def ooc_schedule(M, N, K, elem_bytes, beta_nonzero, budget, opts=None):
                         read_slot=[e.read_slot[r] for r in range(e.nreads)],
                         read_tag=[tuple(e.read_tag[r]) for r in range(e.nreads)]))
     return out
+
+
+def _fp(a):
+    return ctypes.cast(ctypes.c_void_p(_ptr(a)), ctypes.POINTER(ctypes.c_float))
+
+
+def ooc_plan_candidates(M, N, K, elem_bytes, beta_nonzero, budget, opts=None, capacity=32):
+    """C ABI ooc_plan_candidates; returns a list of ooc_plan_candidate."""
+    lib = load()
+    f = lib.ooc_plan_candidates
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_int64] * 3 + [ctypes.c_int32, ctypes.c_int32, ctypes.c_size_t, ctypes.POINTER(ooc_opts),
+                                         ctypes.POINTER(ooc_plan_candidate), ctypes.c_int32,
+                                         ctypes.POINTER(ctypes.c_int32)]
+    buf = (ooc_plan_candidate * capacity)()
+    n = ctypes.c_int32(0)
+    _check(f(M, N, K, elem_bytes, int(bool(beta_nonzero)), budget, ctypes.byref(opts) if opts is not None else None,
+             buf, capacity, ctypes.byref(n)), "ooc_plan_candidates")
+    return [buf[i] for i in range(n.value)]
+
+
+def ooc_autotune(desc, elem_bytes, budget, opts=None, max_candidates=16):
+    """C ABI ooc_autotune; returns [(candidate, seconds)] in candidate order."""
+    lib = load()
+    f = lib.ooc_autotune
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.POINTER(ooc_gemm_desc), ctypes.c_int32, ctypes.c_size_t, ctypes.POINTER(ooc_opts),
+                  ctypes.c_int32, ctypes.POINTER(ooc_plan_candidate), ctypes.POINTER(ctypes.c_double),
+                  ctypes.POINTER(ctypes.c_int32)]
+    buf = (ooc_plan_candidate * max_candidates)()
+    sec = (ctypes.c_double * max_candidates)()
+    n = ctypes.c_int32(0)
+    _check(f(ctypes.byref(desc), elem_bytes, budget, ctypes.byref(opts) if opts is not None else None,
+             max_candidates, buf, sec, ctypes.byref(n)), "ooc_autotune")
+    return [(buf[i], sec[i]) for i in range(n.value)]
+
+
+def ooc_mlp_forward(params, X):
+    """C ABI ooc_mlp_forward on float32 numpy arrays; returns predictions."""
+    import numpy as np
+    lib = load()
+    params = np.ascontiguousarray(params, dtype=np.float32)
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    y = np.empty(X.shape[0], dtype=np.float32)
+    f = lib.ooc_mlp_forward
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
+    _check(f(params.ctypes.data, X.ctypes.data, X.shape[0], y.ctypes.data), "ooc_mlp_forward")
+    return y
+
+
+def ooc_mlp_loss_grad(params, X, t):
+    """C ABI ooc_mlp_loss_grad; returns (loss, grad)."""
+    import numpy as np
+    lib = load()
+    params = np.ascontiguousarray(params, dtype=np.float32)
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    t = np.ascontiguousarray(t, dtype=np.float32)
+    g = np.empty_like(params)
+    loss = ctypes.c_float(0)
+    f = lib.ooc_mlp_loss_grad
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int64, ctypes.c_void_p, ctypes.POINTER(ctypes.c_float)]
+    _check(f(params.ctypes.data, X.ctypes.data, t.ctypes.data, X.shape[0], g.ctypes.data, ctypes.byref(loss)),
+           "ooc_mlp_loss_grad")
+    return loss.value, g
+
+
+def ooc_mlp_train(params, X, t, epochs=200, batch=64, lr=3e-3, seed=1, weight_decay=0.0):
+    """C ABI ooc_mlp_train; returns (trained params, final loss)."""
+    import numpy as np
+    lib = load()
+    p = np.array(params, dtype=np.float32, copy=True)
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    t = np.ascontiguousarray(t, dtype=np.float32)
+    loss = ctypes.c_float(0)
+    f = lib.ooc_mlp_train
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
+                                          ctypes.c_float, ctypes.c_uint64, ctypes.POINTER(ctypes.c_float)]
+    _check(f(p.ctypes.data, X.ctypes.data, t.ctypes.data, X.shape[0], epochs, batch, lr, weight_decay, seed,
+             ctypes.byref(loss)), "ooc_mlp_train")
+    return p, loss.value
+
+
+def ooc_costmodel_set(params):
+    """C ABI ooc_costmodel_set (None clears)."""
+    import numpy as np
+    lib = load()
+    f = lib.ooc_costmodel_set
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int64]
+    if params is None:
+        _check(f(None, 0), "ooc_costmodel_set")
+        return
+    global _model_keepalive
+    _model_keepalive = np.ascontiguousarray(params, dtype=np.float32)
+    _check(f(_model_keepalive.ctypes.data, _model_keepalive.size), "ooc_costmodel_set")
+
+
+_model_keepalive = None
 
 
 def ooc_query_device():

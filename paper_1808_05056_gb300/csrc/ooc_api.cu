@@ -95,6 +95,25 @@ int encode_map_2d(void* map_out, int dtype, const void* base, uint64_t inner, ui
     return OOC_OK;
 }
 
+// installed schedule cost model (ooc_costmodel_set)
+static std::mutex g_model_mu;
+static std::vector<float> g_model;
+
+bool costmodel_get(std::vector<float>& params)
+{
+    std::lock_guard<std::mutex> lk(g_model_mu);
+    if (g_model.empty()) return false;
+    params = g_model;
+    return true;
+}
+
+void costmodel_set(const float* params, int64_t n)
+{
+    std::lock_guard<std::mutex> lk(g_model_mu);
+    if (!params || n <= 0) g_model.clear();
+    else g_model.assign(params, params + n);
+}
+
 int encode_map_3d_bf16(void* map_out, const void* base, uint64_t inner, uint64_t rows, uint64_t planes,
                        uint32_t box_inner, uint32_t box_rows, std::string& why)
 {
@@ -798,6 +817,100 @@ int ooc_dgemm_batched(int32_t count, const ooc_gemm_desc* descs, size_t device_b
                       ooc_stats* stats)
 {
     return run_batched(count, descs, device_budget_bytes, opts, stats);
+}
+
+int ooc_plan_candidates(int64_t M, int64_t N, int64_t K, int32_t elem_bytes, int32_t beta_nonzero, size_t budget,
+                        const ooc_opts* opts_in, ooc_plan_candidate* out, int32_t capacity, int32_t* count)
+{
+    if ((elem_bytes != 4 && elem_bytes != 8) || M <= 0 || N <= 0 || K < 0 || !count || capacity < 0 ||
+        (capacity > 0 && !out))
+        return fail(OOC_ERR_INVALID_ARG, "ooc_plan_candidates: bad arguments");
+    ooc_opts opts;
+    std::memset(&opts, 0, sizeof(opts));
+    if (opts_in) opts = *opts_in;
+    PlanRequest rq{M, N, K, elem_bytes, beta_nonzero != 0, false, false, budget, opts};
+    double hg = 0, dg = 0;
+    if (ooc_query_device(nullptr, &hg, &dg) == OOC_OK && hg > 0 && dg > 0) { rq.h2d_gbps = hg; rq.d2h_gbps = dg; }
+    cudaGetLastError();
+    std::vector<Plan> c;
+    std::string why;
+    int rc = plan_candidates(rq, std::max(capacity, 1), c, why);
+    if (rc) return fail(rc, why);
+    *count = (int32_t)std::min<size_t>(c.size(), (size_t)capacity);
+    for (int32_t i = 0; i < *count; ++i) {
+        ooc_plan_candidate& d = out[i];
+        std::memset(&d, 0, sizeof(d));
+        d.mb = c[i].mb; d.nb = c[i].nb; d.kb = c[i].kb;
+        d.depth = c[i].nA; d.b_buffers = c[i].nB; d.c_buffers = c[i].nC;
+        d.est_seconds = c[i].est_seconds;
+        plan_features(c[i], rq, d.features);
+    }
+    return OOC_OK;
+}
+
+int ooc_autotune(const ooc_gemm_desc* d, int32_t elem_bytes, size_t budget, const ooc_opts* opts_in,
+                 int32_t max_candidates, ooc_plan_candidate* out, double* seconds_out, int32_t* count)
+{
+    if (!d || !out || !seconds_out || !count || max_candidates <= 0 || (elem_bytes != 4 && elem_bytes != 8))
+        return fail(OOC_ERR_INVALID_ARG, "ooc_autotune: bad arguments");
+    ooc_opts opts;
+    std::memset(&opts, 0, sizeof(opts));
+    if (opts_in) opts = *opts_in;
+    int32_t n = 0;
+    int rc = ooc_plan_candidates(d->M, d->N, d->K, elem_bytes, d->beta != 0.0, budget, &opts, out, max_candidates, &n);
+    if (rc) return rc;
+    Operands o{d->A, d->lda, d->B, d->ldb, d->C, d->ldc, d->alpha, d->beta};
+    for (int32_t i = -1; i < n; ++i) {  // i = -1: untimed warm-up with the first candidate
+        const ooc_plan_candidate& c = out[std::max(i, 0)];
+        ooc_opts oc = opts;
+        oc.mb = c.mb; oc.nb = c.nb; oc.kb = c.kb;
+        oc.depth = c.depth; oc.c_buffers = c.c_buffers; oc.b_buffers = c.b_buffers;
+        oc.flags &= ~(OOC_PLAN_MODEL | OOC_PLAN_PAPER);
+        ooc_stats st;
+        rc = run_ooc(d->transA, d->transB, d->M, d->N, d->K, o, elem_bytes, budget, &oc, &st);
+        if (rc) return rc;
+        if (i >= 0) seconds_out[i] = st.device_seconds;
+    }
+    *count = n;
+    return OOC_OK;
+}
+
+int ooc_mlp_forward(const float* params, const float* X, int64_t n, float* y)
+{
+    if (!params || (n > 0 && (!X || !y)) || n < 0) return fail(OOC_ERR_INVALID_ARG, "ooc_mlp_forward: bad arguments");
+    std::string why;
+    int rc = check_device(why);
+    if (rc) return fail(rc, why);
+    rc = mlp_forward_host(params, X, n, y, why);
+    return rc ? fail(rc, why) : OOC_OK;
+}
+
+int ooc_mlp_loss_grad(const float* params, const float* X, const float* t, int64_t n, float* grad, float* loss)
+{
+    if (!params || !X || !t || !grad || !loss || n <= 0) return fail(OOC_ERR_INVALID_ARG, "ooc_mlp_loss_grad: bad arguments");
+    std::string why;
+    int rc = check_device(why);
+    if (rc) return fail(rc, why);
+    rc = mlp_loss_grad_host(params, X, t, n, grad, loss, why);
+    return rc ? fail(rc, why) : OOC_OK;
+}
+
+int ooc_mlp_train(float* params, const float* X, const float* t, int64_t n, int32_t epochs, int32_t batch, float lr,
+                  float weight_decay, uint64_t seed, float* final_loss)
+{
+    if (!params || !X || !t || n <= 0) return fail(OOC_ERR_INVALID_ARG, "ooc_mlp_train: bad arguments");
+    std::string why;
+    int rc = check_device(why);
+    if (rc) return fail(rc, why);
+    rc = mlp_train_host(params, X, t, n, epochs, batch, lr, weight_decay, seed, final_loss, why);
+    return rc ? fail(rc, why) : OOC_OK;
+}
+
+int ooc_costmodel_set(const float* params, int64_t n)
+{
+    if (params && n != kMlpParams) return fail(OOC_ERR_INVALID_ARG, "cost model needs OOC_MLP_PARAMS floats");
+    costmodel_set(params, n);
+    return OOC_OK;
 }
 
 const char* ooc_strerror(int code)

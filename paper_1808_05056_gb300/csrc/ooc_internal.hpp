@@ -54,7 +54,24 @@ struct PlanRequest {
 };
 
 // Returns OOC_OK and fills `plan`, or an error code with a message in `why`.
+// With OOC_PLAN_MODEL in rq.opts.flags and a cost model installed, the plan is
+// the candidate with the smallest predicted time; otherwise the heuristic best.
 int make_plan(const PlanRequest& rq, Plan& plan, std::string& why);
+
+// The best `max_n` distinct candidate plans by the heuristic estimate (fitting the budget).
+int plan_candidates(const PlanRequest& rq, int max_n, std::vector<Plan>& out, std::string& why);
+
+// --- schedule cost model (mlp.cu, plan.cpp) ---------------------------------
+constexpr int kMlpIn = 16;
+constexpr int kMlpParams = 64 * 16 + 64 + 64 * 64 + 64 + 64 + 1;
+void plan_features(const Plan& p, const PlanRequest& rq, float* f);
+int mlp_forward_host(const float* params, const float* X, int64_t n, float* y, std::string& why);
+int mlp_loss_grad_host(const float* params, const float* X, const float* t, int64_t n, float* grad, float* loss,
+                       std::string& why);
+int mlp_train_host(float* params, const float* X, const float* t, int64_t n, int epochs, int batch, float lr,
+                   float wd, uint64_t seed, float* final_loss, std::string& why);
+bool costmodel_get(std::vector<float>& params);
+void costmodel_set(const float* params, int64_t n);
 
 // -------------------------------------------------------------- schedule --
 enum OpKind { kH2D = 0, kKernel = 1, kD2H = 2, kRecord = 3, kWait = 4 };

@@ -207,6 +207,8 @@ bool paper_plan(const PlanRequest& rq, Plan& best, std::string& why)
 
 }  // namespace
 
+static thread_local std::vector<Plan>* collect_ = nullptr;
+
 int make_plan(const PlanRequest& rq, Plan& p, std::string& why)
 {
     p = Plan{};
@@ -280,10 +282,12 @@ int make_plan(const PlanRequest& rq, Plan& p, std::string& why)
     bool found = false;
     Plan best;
     double best_t = std::numeric_limits<double>::infinity();
+    std::vector<Plan>* keep = collect_;  // candidate collection (plan_candidates)
     for (int64_t kb : kbs) {
         const int64_t nkc = rq.K == 0 ? 1 : cdiv(rq.K, kb);
         std::vector<int> nBs = {(int)std::min<int64_t>(2 * nkc, 1 << 20), (int)nkc};
         if (nkc > 2) nBs.push_back(2);
+        if (rq.opts.b_buffers > 0) nBs = {rq.opts.b_buffers};
         for (int64_t mb : mbs)
             for (int64_t nb : nbs)
                 for (int nA : nAs)
@@ -297,6 +301,7 @@ int make_plan(const PlanRequest& rq, Plan& p, std::string& why)
                             if (c.device_bytes > rq.budget) continue;
                             traffic(c);
                             c.est_seconds = estimate(c, f, sms, rq.h2d_gbps, rq.d2h_gbps);
+                            if (keep) keep->push_back(c);
                             // prefer faster; near-ties go to fewer device bytes
                             if (!found || c.est_seconds < best_t * (1 - 1e-9) ||
                                 (c.est_seconds <= best_t * (1 + 1e-9) && c.device_bytes < best.device_bytes)) {
@@ -309,7 +314,69 @@ int make_plan(const PlanRequest& rq, Plan& p, std::string& why)
         return OOC_ERR_BUDGET;
     }
     p = best;
+    if (!keep && (rq.opts.flags & OOC_PLAN_MODEL)) {
+        std::vector<float> params;
+        if (costmodel_get(params)) {
+            std::vector<Plan> cands;
+            std::string w2;
+            if (plan_candidates(rq, 64, cands, w2) == OOC_OK && !cands.empty()) {
+                std::vector<float> X(cands.size() * kMlpIn), y(cands.size());
+                for (size_t i = 0; i < cands.size(); ++i) plan_features(cands[i], rq, &X[i * kMlpIn]);
+                if (mlp_forward_host(params.data(), X.data(), (int64_t)cands.size(), y.data(), w2) == OOC_OK) {
+                    size_t bi = 0;
+                    for (size_t i = 1; i < cands.size(); ++i)
+                        if (y[i] < y[bi]) bi = i;
+                    p = cands[bi];
+                }
+            }
+        }
+    }
     return OOC_OK;
+}
+
+int plan_candidates(const PlanRequest& rq, int max_n, std::vector<Plan>& out, std::string& why)
+{
+    std::vector<Plan> all;
+    collect_ = &all;
+    Plan best;
+    PlanRequest r2 = rq;
+    r2.opts.flags &= ~OOC_PLAN_MODEL;
+    const int rc = make_plan(r2, best, why);
+    collect_ = nullptr;
+    if (rc) return rc;
+    std::stable_sort(all.begin(), all.end(), [](const Plan& a, const Plan& b) { return a.est_seconds < b.est_seconds; });
+    out.clear();
+    for (const Plan& c : all) {
+        bool dup = false;
+        for (const Plan& o : out)
+            if (o.mb == c.mb && o.nb == c.nb && o.kb == c.kb && o.nA == c.nA && o.nB == c.nB && o.nC == c.nC) dup = true;
+        if (!dup) out.push_back(c);
+        if ((int)out.size() >= max_n) break;
+    }
+    if (out.empty()) out.push_back(best);
+    return OOC_OK;
+}
+
+// Cost-model inputs: problem scale and form, the plan's block / chunk / ring
+// sizes, and three quantities the analytic estimate models coarsely: the wave
+// efficiency of a full block's tiles on the device, the share of operand
+// copies that are narrow strided rows, and the estimate itself.
+void plan_features(const Plan& p, const PlanRequest& rq, float* f)
+{
+    auto lg = [](double x) { return (float)std::log2(std::max(x, 1.0)); };
+    const FormModel fm = form_model(p.form, p.es, p.K, p.slices);
+    const double slots = (double)device_sm_count() * fm.ctas_per_sm;
+    const double tiles = (double)cdiv(p.mb, fm.tile_m) * cdiv(p.nb, fm.tile_n);
+    const double waves = std::ceil(tiles / slots);
+    f[0] = lg((double)p.M) / 16; f[1] = lg((double)p.N) / 16; f[2] = lg((double)std::max<int64_t>(p.K, 1)) / 16;
+    f[3] = p.form == OOC_FORM_FP64; f[4] = p.form == OOC_FORM_OZAKI; f[5] = p.form == OOC_FORM_BF16X3;
+    f[6] = lg((double)rq.budget) / 40;
+    f[7] = (float)(tiles / (waves * slots));
+    f[8] = lg((double)p.mb) / 16; f[9] = lg((double)p.nb) / 16; f[10] = lg((double)p.kb) / 16;
+    f[11] = p.nA / 3.0f; f[12] = lg((double)p.nB + 1) / 8;
+    f[13] = (narrow_rows(p, kMatA) + narrow_rows(p, kMatB) + narrow_rows(p, kMatC)) / 3.0f;
+    f[14] = lg((double)(p.h * p.w * p.nkc)) / 16;
+    f[15] = (float)(std::log2(std::max(p.est_seconds, 1e-9)) / 10.0);
 }
 
 size_t slot_offset(const Plan& p, int32_t s)
