@@ -164,7 +164,9 @@ int ooc_dgemm_batched(int32_t count, const ooc_gemm_desc* descs, size_t device_b
  * In-core device GEMM (the paper's runtime DGEMM call of the pipeline's
  * compute stage): C = alpha * op(A) * op(B) + beta * C on device pointers,
  * FP64, enqueued on `stream` (a cudaStream_t, NULL = legacy default stream)
- * and not synchronised.  Same layout rules as ooc_dgemm; no allocation.
+ * and not synchronised.  Same layout rules as ooc_dgemm, plus 16-byte aligned
+ * device bases and even leading dimensions (else OOC_ERR_UNSUPPORTED); the
+ * first call allocates a 4-byte device error word kept for the process.
  */
 int ooc_dgemm_device(char transA, char transB, int64_t M, int64_t N, int64_t K, double alpha,
                      const double* dA, int64_t lda, const double* dB, int64_t ldb, double beta,
