@@ -260,6 +260,7 @@ struct Exec {
     cudaStream_t smap[3] = {nullptr, nullptr, nullptr};  // schedule stream id -> stream for the current plan
     int ev_base = 0;           // offset of the current plan's events in ev
     bool time_kernels = true;  // record timing events around tile launches (not inside graph capture)
+    uint32_t flags = 0;        // ooc_opts.flags of the call
     double h2d = 0, d2h = 0;
     long n_copy = 0, n_kern = 0;
     std::vector<cudaEvent_t> ev;
@@ -389,6 +390,7 @@ int launch_split_tile(const Plan& p, const Op& op, Exec& x, const Operands& o, i
     P.ldc = p.ldc_dev;
     P.err = err;
     P.kblock = 64;
+    P.pair = (x.flags & OOC_TC_PAIR) != 0;
     ++x.launches;
     return launch_tc_terms(P, st, why);
 }
@@ -531,6 +533,7 @@ int run_ooc(char ta, char tb, int64_t M, int64_t N, int64_t K, const Operands& o
         rq.d2h_gbps = dg;
     }
     Exec x;
+    x.flags = opts.flags;
     rc = make_plan(rq, x.p, why);
     if (rc) return fail(rc, why);
     const Plan& p = x.p;
@@ -682,6 +685,7 @@ int run_batched(int32_t count, const ooc_gemm_desc* d, size_t budget, const ooc_
 
     Inject inj;
     Exec x;
+    x.flags = opts.flags;
     if (opts.workspace) {
         if (opts.workspace_bytes < 2 * half + 256) return fail(OOC_ERR_INVALID_ARG, "workspace smaller than the budget");
         x.arena = static_cast<char*>(opts.workspace);

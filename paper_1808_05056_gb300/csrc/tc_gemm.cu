@@ -51,11 +51,13 @@ namespace ooc {
 namespace {
 
 constexpr int BM = 128, BN = 128;
-constexpr uint32_t RING_BYTES = 192u * 1024u;
+constexpr uint32_t RING_BYTES = 192u * 1024u;       // single-CTA stage ring
+constexpr uint32_t RING_BYTES_PAIR = 216u * 1024u;  // pair stage ring (three 72 KiB BF16x3 stages)
 constexpr int EPI_WARPS = 16;            // 4 per TMEM lane quadrant, 32 columns each
 constexpr int THREADS = (2 + EPI_WARPS) * 32;
 constexpr int MAX_GROUPS = 64;
 constexpr size_t SMEM_BYTES = 1024 + RING_BYTES + 1024;
+constexpr size_t SMEM_BYTES_PAIR = 1024 + RING_BYTES_PAIR + 1024;
 
 struct TcGroup {
     int8_t na, nb, np, pad0;
@@ -119,19 +121,29 @@ __device__ __forceinline__ double scaled_f32_to_f64(uint32_t xb, int e)
 // DF32 = false (Ozaki): each of the group's (at most two) pairs has its own
 // accumulator of exact integer partial sums, drained into FP64 with its
 // power-of-two weight; the two pairs share the A digit plane.
-// BK: K block of one stage, 64 (128-byte swizzle) or 32 (64-byte swizzle) bf16.
-template <bool DF32, int BK>
+// BK: K block of one stage (64 bf16, 128-byte swizzle).
+// PAIR: two CTAs of a cluster compute one 256 x 128 tile with cta_group::2
+// MMAs issued by rank 0: each CTA loads its 128 rows of every A plane tile and
+// 64 of the 128 rows of every B plane tile, so a CTA moves and reads a quarter
+// less per MMA than a single-CTA 128 x 128 tile and the ring holds a third
+// stage for BF16x3.  Rank 1's copies complete on rank 0's stage barriers; the
+// MMA completions are multicast to both CTAs; both CTAs' epilogues report a
+// drained accumulator to rank 0.
+template <bool DF32, int BK, bool PAIR>
 __global__ void __launch_bounds__(THREADS, 1) tc_terms_kernel(const __grid_constant__ CUtensorMap tmA,
                                                               const __grid_constant__ CUtensorMap tmB,
                                                               const __grid_constant__ TcArgs p)
 {
-    constexpr uint32_t TILE_BYTES = 128u * BK * 2u;  // one plane tile: 128 rows x BK bf16
+    constexpr uint32_t A_TILE = 128u * BK * 2u;                  // 128 rows x BK bf16
+    constexpr uint32_t B_TILE = (PAIR ? 64u : 128u) * BK * 2u;   // this CTA's rows of a B tile
+    constexpr uint32_t RING = PAIR ? RING_BYTES_PAIR : RING_BYTES;
+    constexpr int PM = PAIR ? 2 * BM : BM;                       // C rows per tile
     constexpr uint32_t kAccCols = 2 * BN;  // TMEM columns of one buffer: accumulators 0 and 1
     constexpr uint32_t kTmemCols = 2 * kAccCols;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* ring = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                            ~uintptr_t(1023));
-    uint64_t* full = reinterpret_cast<uint64_t*>(ring + RING_BYTES);
+    uint64_t* full = reinterpret_cast<uint64_t*>(ring + RING);
     uint64_t* empty = full + 16;
     uint64_t* acc_full = empty + 16;
     uint64_t* acc_empty = acc_full + 2;
@@ -139,9 +151,18 @@ __global__ void __launch_bounds__(THREADS, 1) tc_terms_kernel(const __grid_const
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = PAIR ? cluster_ctarank() : 0u;
+    const bool leader = rank == 0;
+    const int unit0 = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;  // tile-walking unit (CTA or pair)
+    const int nunits = PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
     if (warp == 1) {
-        tmem_alloc(tmem_slot, kTmemCols);
-        tmem_relinquish();
+        if constexpr (PAIR) {
+            tmem_alloc_pair(tmem_slot, kTmemCols);
+            tmem_relinquish_pair();
+        } else {
+            tmem_alloc(tmem_slot, kTmemCols);
+            tmem_relinquish();
+        }
     }
     if (threadIdx.x == 0) {
         for (int s = 0; s < p.nstages; ++s) {
@@ -150,29 +171,31 @@ __global__ void __launch_bounds__(THREADS, 1) tc_terms_kernel(const __grid_const
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&acc_full[b], 1);
-            mbar_init(&acc_empty[b], EPI_WARPS);
+            mbar_init(&acc_empty[b], EPI_WARPS * (PAIR ? 2 : 1));
         }
         mbar_init(drain, 1);
         mbar_fence_init();
     }
     tc_fence_before();
-    __syncthreads();
+    if constexpr (PAIR) cluster_sync_all(); else __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
 
-    const int64_t my_tiles = p.tiles > (int)blockIdx.x ? (p.tiles - 1 - (int)blockIdx.x) / gridDim.x + 1 : 0;
+    const int64_t my_tiles = p.tiles > unit0 ? (p.tiles - 1 - unit0) / nunits + 1 : 0;
 
     if (warp == 0) {
-        // ------------------------------------------------ TMA producer
+        // ------------------------------------------------ TMA producer (each CTA loads its own halves)
         if (lane == 0) {
             tma_prefetch_desc(&tmA);
             tma_prefetch_desc(&tmB);
             uint32_t it = 0;
             bool ok = true;
             for (int64_t tl = 0; tl < my_tiles && ok; ++tl) {
-                const int tile = (int)blockIdx.x + (int)tl * (int)gridDim.x;
+                const int tile = unit0 + (int)tl * nunits;
                 int tm, tn;
                 tile_coords(tile, p.tiles_m, p.tiles_n, tm, tn);
+                const int arow = tm * PM + (int)rank * BM;
+                const int brow = tn * BN + (PAIR ? (int)rank * (BN / 2) : 0);
                 for (int c = 0; c < p.nchunks && ok; ++c) {
                     const int kb0 = c * p.chunk_kblocks, kb1 = min(p.kblocks, kb0 + p.chunk_kblocks);
                     for (int gi = 0; gi < p.ngroups && ok; ++gi) {
@@ -182,17 +205,29 @@ __global__ void __launch_bounds__(THREADS, 1) tc_terms_kernel(const __grid_const
                             const uint32_t ph = (it / (uint32_t)p.nstages) & 1u;
                             if (!mbar_wait(&empty[s], ph ^ 1u, p.err, kErrWaitEmpty)) { ok = false; break; }
                             unsigned char* st = ring + (size_t)s * p.stage_bytes;
-                            mbar_arrive_expect_tx(&full[s], (uint32_t)(g.na + g.nb) * TILE_BYTES);
-                            for (int a = 0; a < g.na; ++a)
-                                tma_load_3d(st + a * TILE_BYTES, &tmA, &full[s], kb * BK, tm * BM, g.aplane[a]);
-                            for (int b = 0; b < g.nb; ++b)
-                                tma_load_3d(st + (g.na + b) * TILE_BYTES, &tmB, &full[s], kb * BK, tn * BN,
-                                            g.bplane[b]);
+                            const uint32_t bytes = (uint32_t)g.na * A_TILE + (uint32_t)g.nb * B_TILE;
+                            if constexpr (PAIR) {
+                                // rank 0's barrier counts both CTAs' bytes; both CTAs' copies complete on it
+                                if (leader) mbar_arrive_expect_tx(&full[s], 2u * bytes);
+                                const uint32_t bar = mapa_shared(smem_u32(&full[s]), 0);
+                                for (int a = 0; a < g.na; ++a)
+                                    tma_load_3d_pair(st + a * A_TILE, &tmA, bar, kb * BK, arow, g.aplane[a]);
+                                for (int b = 0; b < g.nb; ++b)
+                                    tma_load_3d_pair(st + g.na * A_TILE + b * B_TILE, &tmB, bar, kb * BK, brow,
+                                                     g.bplane[b]);
+                            } else {
+                                mbar_arrive_expect_tx(&full[s], bytes);
+                                for (int a = 0; a < g.na; ++a)
+                                    tma_load_3d(st + a * A_TILE, &tmA, &full[s], kb * BK, arow, g.aplane[a]);
+                                for (int b = 0; b < g.nb; ++b)
+                                    tma_load_3d(st + g.na * A_TILE + b * B_TILE, &tmB, &full[s], kb * BK, brow,
+                                                g.bplane[b]);
+                            }
                         }
                     }
                 }
             }
-            if (!ok) {
+            if (!ok && (!PAIR || leader)) {
                 // let the copies already issued land before the CTA exits
                 const uint32_t first = it > (uint32_t)p.nstages ? it - (uint32_t)p.nstages : 0u;
                 for (uint32_t q = first; q < it; ++q) {
@@ -205,9 +240,9 @@ __global__ void __launch_bounds__(THREADS, 1) tc_terms_kernel(const __grid_const
             }
         }
     } else if (warp == 1) {
-        // ------------------------------------------------ MMA issuer
-        if (lane == 0) {
-            const uint32_t idesc = idesc_bf16_f32(BM, BN);
+        // ------------------------------------------------ MMA issuer (rank 0 of a pair)
+        if (lane == 0 && leader) {
+            const uint32_t idesc = idesc_bf16_f32(PM, BN);
             uint32_t it = 0, unit = 0;
             bool ok = true;
             for (int64_t tl = 0; tl < my_tiles && ok; ++tl) {
@@ -232,26 +267,31 @@ __global__ void __launch_bounds__(THREADS, 1) tc_terms_kernel(const __grid_const
                             tc_fence_after();
                             const uint32_t st = smem_u32(ring + (size_t)s * p.stage_bytes);
                             for (int q = 0; q < g.np; ++q) {
-                                const uint32_t a0 = st + (uint32_t)g.pa[q] * TILE_BYTES;
-                                const uint32_t b0 = st + (uint32_t)(g.na + g.pb[q]) * TILE_BYTES;
+                                const uint32_t a0 = st + (uint32_t)g.pa[q] * A_TILE;
+                                const uint32_t b0 = st + (uint32_t)g.na * A_TILE + (uint32_t)g.pb[q] * B_TILE;
                                 const bool second = q > 0;
                                 const uint32_t d = second ? d_tmem + BN : d_tmem;
 #pragma unroll
                                 for (int k = 0; k < BK / 16; ++k) {
-                                    const uint64_t da = BK == 64 ? sw128_kmajor_desc(a0 + k * 32) : sw64_kmajor_desc(a0 + k * 32);
-                                    const uint64_t db = BK == 64 ? sw128_kmajor_desc(b0 + k * 32) : sw64_kmajor_desc(b0 + k * 32);
-                                    tc_mma_bf16(d, da, db, idesc, second ? accumulate2 : accumulate);
+                                    const uint64_t da = sw128_kmajor_desc(a0 + k * 32);
+                                    const uint64_t db = sw128_kmajor_desc(b0 + k * 32);
+                                    if constexpr (PAIR)
+                                        tc_mma_bf16_pair(d, da, db, idesc, second ? accumulate2 : accumulate);
+                                    else
+                                        tc_mma_bf16(d, da, db, idesc, second ? accumulate2 : accumulate);
                                     if (second) accumulate2 = 1; else accumulate = 1;
                                 }
                             }
-                            tc_commit(&empty[s]);
+                            if constexpr (PAIR) tc_commit_pair(&empty[s], 3); else tc_commit(&empty[s]);
                         }
-                        if (ok) tc_commit(&acc_full[buf]);
+                        if (ok) {
+                            if constexpr (PAIR) tc_commit_pair(&acc_full[buf], 3); else tc_commit(&acc_full[buf]);
+                        }
                     }
                 }
             }
             // every MMA issued so far has completed before TMEM is released
-            tc_commit(drain);
+            if constexpr (PAIR) tc_commit_pair(drain, 1); else tc_commit(drain);
             const uint64_t t0 = globaltimer_ns();
             while (!mbar_try_wait(smem_u32(drain), 0u) && globaltimer_ns() - t0 < kWaitLimitNs) {
             }
@@ -260,7 +300,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_terms_kernel(const __grid_const
         // ------------------------------------------------ epilogue warps
         const int q = warp & 3;                 // TMEM lane quadrant this warp may access
         const int quarter = (warp - 2) >> 2;    // column quarter of the tile
-        const int row_in_tile = q * 32 + lane;
+        const int row_in_tile = (int)rank * BM + q * 32 + lane;
         const uint32_t lane_off = (uint32_t)(q * 32) << 16;
         // DF32: a double-float (hi, lo) per output; FP64: one double per output
         float hi[DF32 ? 32 : 1], lo[DF32 ? 32 : 1];
@@ -272,7 +312,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_terms_kernel(const __grid_const
         uint32_t unit = 0;
         bool ok = true;
         for (int64_t tl = 0; tl < my_tiles && ok; ++tl) {
-            const int tile = (int)blockIdx.x + (int)tl * (int)gridDim.x;
+            const int tile = unit0 + (int)tl * nunits;
             int tm, tn;
             tile_coords(tile, p.tiles_m, p.tiles_n, tm, tn);
             for (int c = 0; c < p.nchunks && ok; ++c) {
@@ -326,12 +366,15 @@ __global__ void __launch_bounds__(THREADS, 1) tc_terms_kernel(const __grid_const
                     }
                     tc_fence_before();
                     __syncwarp();
-                    if (lane == 0) mbar_arrive(&acc_empty[buf]);
+                    if (lane == 0) {
+                        if constexpr (PAIR) mbar_arrive_cluster(mapa_shared(smem_u32(&acc_empty[buf]), 0));
+                        else mbar_arrive(&acc_empty[buf]);
+                    }
                 }
             }
             if (!ok) break;
             // final epilogue of this tile
-            const int64_t row = (int64_t)tm * BM + row_in_tile;
+            const int64_t row = (int64_t)tm * PM + row_in_tile;
             const int64_t col0 = (int64_t)tn * BN + quarter * 32;
             if (row < p.M) {
                 const int re = p.row_exp ? p.row_exp[row] : 0;
@@ -363,10 +406,11 @@ __global__ void __launch_bounds__(THREADS, 1) tc_terms_kernel(const __grid_const
         }
     }
     tc_fence_before();
-    __syncthreads();
+    if constexpr (PAIR) cluster_sync_all(); else __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc(tmem_base, kTmemCols);
+        if constexpr (PAIR) tmem_dealloc_pair(tmem_base, kTmemCols);
+        else tmem_dealloc(tmem_base, kTmemCols);
     }
 }
 
@@ -496,6 +540,7 @@ __global__ void __launch_bounds__(256) split_ozaki_kernel(const double* __restri
 
 std::once_flag g_attr_once;
 int g_sms = 0;
+int g_pairs = 0;  // resident CTA pairs of the pair kernel (0: pairs unavailable)
 
 }  // namespace
 
@@ -536,15 +581,42 @@ int launch_tc_terms(const TcProblem& P, void* stream, std::string& why)
     if (P.M <= 0 || P.N <= 0) return OOC_OK;
     if (P.ngroups <= 0 || P.ngroups > MAX_GROUPS) { why = "bad group count"; return OOC_ERR_INVALID_ARG; }
     std::call_once(g_attr_once, [] {
-        cudaFuncSetAttribute(tc_terms_kernel<true, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
-        cudaFuncSetAttribute(tc_terms_kernel<false, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+        cudaFuncSetAttribute(tc_terms_kernel<true, 64, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)SMEM_BYTES);
+        cudaFuncSetAttribute(tc_terms_kernel<false, 64, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)SMEM_BYTES);
+        cudaFuncSetAttribute(tc_terms_kernel<true, 64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)SMEM_BYTES_PAIR);
+        cudaFuncSetAttribute(tc_terms_kernel<false, 64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)SMEM_BYTES_PAIR);
         g_sms = device_sm_count();
+        // CTA pairs that can be resident at once (clusters are placed inside GPCs)
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(2 * 76);
+        cfg.blockDim = dim3(THREADS);
+        cfg.dynamicSmemBytes = SMEM_BYTES_PAIR;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 2;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, tc_terms_kernel<true, 64, true>, &cfg) != cudaSuccess) {
+            cudaGetLastError();
+            n = 0;
+        }
+        g_pairs = n;
     });
     // 64-wide K blocks (128-byte swizzle) measured faster than 32-wide ones for
     // both forms on GB300 (BF16x3 166 vs 136, Ozaki 28 vs 18 logical TFLOP/s)
     const int BK = 64;
     if (P.kblock != BK) { why = "only 64-wide K blocks are built"; return OOC_ERR_INVALID_ARG; }
-    const uint32_t TILE_BYTES = 128u * (uint32_t)BK * 2u;
+    const bool pair = P.pair && g_pairs > 0;
+    const uint32_t A_TILE = 128u * (uint32_t)BK * 2u;
+    const uint32_t B_TILE = (pair ? 64u : 128u) * (uint32_t)BK * 2u;
+    const int PM = pair ? 2 * BM : BM;
     TcArgs a;
     std::memset(&a, 0, sizeof(a));
     a.M = (int)P.M; a.N = (int)P.N;
@@ -554,9 +626,9 @@ int launch_tc_terms(const TcProblem& P, void* stream, std::string& why)
     a.nchunks = (a.kblocks + a.chunk_kblocks - 1) / a.chunk_kblocks;
     a.ngroups = P.ngroups;
     a.tiles_n = (int)((P.N + BN - 1) / BN);
-    a.tiles_m = (int)((P.M + BM - 1) / BM);
+    a.tiles_m = (int)((P.M + PM - 1) / PM);
     a.tiles = a.tiles_m * a.tiles_n;
-    int max_tiles = 0;
+    uint32_t max_stage = 0;
     for (int g = 0; g < P.ngroups; ++g) {
         const TcGroupSpec& s = P.groups[g];
         TcGroup& d = a.g[g];
@@ -573,10 +645,10 @@ int launch_tc_terms(const TcProblem& P, void* stream, std::string& why)
             why = "exact (Ozaki) groups hold at most two pairs";
             return OOC_ERR_INVALID_ARG;
         }
-        max_tiles = std::max(max_tiles, s.na + s.nb);
+        max_stage = std::max(max_stage, (uint32_t)s.na * A_TILE + (uint32_t)s.nb * B_TILE);
     }
-    a.stage_bytes = (uint32_t)max_tiles * TILE_BYTES;
-    a.nstages = std::min<int>(16, (int)(RING_BYTES / a.stage_bytes));  // barrier slots: 16
+    a.stage_bytes = max_stage;
+    a.nstages = std::min<int>(16, (int)((pair ? RING_BYTES_PAIR : RING_BYTES) / a.stage_bytes));  // 16 barrier slots
     if (a.nstages < 2) { why = "stage ring too small"; return OOC_ERR_INVALID_ARG; }
     a.alpha = P.alpha; a.beta = P.beta;
     a.read_c = P.read_c ? 1 : 0; a.c_fp32 = P.c_fp32 ? 1 : 0;
@@ -588,18 +660,38 @@ int launch_tc_terms(const TcProblem& P, void* stream, std::string& why)
     std::memset(&ma, 0, sizeof(ma));
     std::memset(&mb, 0, sizeof(mb));
     if (a.kblocks > 0) {  // K == 0 runs the epilogue only (C = beta * C)
+        // rows past the padded planes (the last pair tile) read as zeros from TMA
         int rc = encode_map_3d_bf16(&ma, P.a_planes, (uint64_t)P.k_pad, (uint64_t)P.a_rows_pad,
                                     (uint64_t)P.a_nplanes, BK, BM, why);
         if (rc) return rc;
         rc = encode_map_3d_bf16(&mb, P.b_planes, (uint64_t)P.k_pad, (uint64_t)P.b_rows_pad, (uint64_t)P.b_nplanes,
-                                BK, BN, why);
+                                BK, pair ? BN / 2 : BN, why);
         if (rc) return rc;
     }
-    const int grid = std::min(a.tiles, g_sms > 0 ? g_sms : 152);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (P.df32) tc_terms_kernel<true, 64><<<grid, THREADS, SMEM_BYTES, st>>>(ma, mb, a);
-    else tc_terms_kernel<false, 64><<<grid, THREADS, SMEM_BYTES, st>>>(ma, mb, a);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e;
+    if (pair) {
+        const int pairs = std::min(a.tiles, g_pairs);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(2 * pairs));
+        cfg.blockDim = dim3(THREADS);
+        cfg.dynamicSmemBytes = SMEM_BYTES_PAIR;
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 2;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        e = P.df32 ? cudaLaunchKernelEx(&cfg, tc_terms_kernel<true, 64, true>, ma, mb, a)
+                   : cudaLaunchKernelEx(&cfg, tc_terms_kernel<false, 64, true>, ma, mb, a);
+    } else {
+        const int grid = std::min(a.tiles, g_sms > 0 ? g_sms : 152);
+        if (P.df32) tc_terms_kernel<true, 64, false><<<grid, THREADS, SMEM_BYTES, st>>>(ma, mb, a);
+        else tc_terms_kernel<false, 64, false><<<grid, THREADS, SMEM_BYTES, st>>>(ma, mb, a);
+        e = cudaGetLastError();
+    }
     if (e != cudaSuccess) { why = std::string("tc_terms launch: ") + cudaGetErrorString(e); return OOC_ERR_CUDA; }
     return OOC_OK;
 }
