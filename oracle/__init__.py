@@ -6,6 +6,8 @@ product library never does, and it shares no code with it.
 
 Contents
   oracle.c        plain FP64 triple-loop GEMM (Section IV problem statement)
+  factor.c        plain FP64 triangular solve and Cholesky (Section VII's next step)
+  level3.py       SYRK / GEMMT / TRSM / POTRF on numpy operands
   partition.py    the paper's matrix partitioner, read from Section IV
   pipeline.py     the Section IV buffer-hazard rule, as a timeline checker
   costmodel.py    FP64 reference of the schedule cost-model MLP
@@ -18,18 +20,19 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "factor.c")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
 
 def build(force=False):
-    """Compile oracle.c with the host C compiler (no FMA contraction)."""
+    """Compile oracle.c and factor.c with the host C compiler (no FMA contraction)."""
     if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+            and all(os.path.getmtime(_LIB) >= os.path.getmtime(f) for f in _SRCS)):
         return _LIB
     tmp = _LIB + ".%d.tmp" % os.getpid()
-    subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-ffp-contract=off",
-                           _SRC, "-o", tmp, "-lpthread"])
+    subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-ffp-contract=off"] + _SRCS +
+                          ["-o", tmp, "-lpthread", "-lm"])
     os.replace(tmp, _LIB)
     return _LIB
 
@@ -49,6 +52,10 @@ def load(path=None):
         f = getattr(lib, name)
         f.restype = ctypes.c_int
         f.argtypes = blk
+    lib.oracle_dtrsm.restype = ctypes.c_int
+    lib.oracle_dtrsm.argtypes = [ctypes.c_char] * 4 + [i64, i64, dbl, vp, i64, vp, i64, ctypes.c_int]
+    lib.oracle_dpotrf.restype = i64
+    lib.oracle_dpotrf.argtypes = [ctypes.c_char, i64, vp, i64, ctypes.c_int]
     lib.oracle_dgemm.restype = ctypes.c_int
     lib.oracle_dgemm.argtypes = [ctypes.c_char, ctypes.c_char, i64, i64, i64, dbl, vp, i64, vp,
                                  i64, dbl, vp, i64, ctypes.c_int]

@@ -49,8 +49,9 @@ def _build_variant(tmp_path, name, old, new):
     d.mkdir()
     (d / "o.c").write_text(src)
     lib = str(d / "libo.so")
+    factor = os.path.join(os.path.dirname(SRC), "factor.c")
     subprocess.check_call(["gcc", "-O1", "-fPIC", "-shared", "-std=c11", "-ffp-contract=off",
-                           str(d / "o.c"), "-o", lib, "-lpthread"])
+                           str(d / "o.c"), factor, "-o", lib, "-lpthread", "-lm"])
     return oracle.load(lib)
 
 
