@@ -197,6 +197,72 @@ int ooc_dgemm_noalloc(char transA, char transB, int64_t M, int64_t N, int64_t K,
                       const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
                       double* C, int64_t ldc, size_t device_budget_bytes, void* stream);
 
+/* ---- level-3 operations beyond GEMM ------------------------------------ */
+/* Section VII of the paper names the rest of level-3 BLAS as the next step
+ * for the out-of-core pipeline; these run through the same planner, schedule
+ * and tile kernels as ooc_dgemm. */
+
+/*
+ * GEMMT: C = alpha * op(A) * op(B) + beta * C on one triangle of the N x N
+ * matrix C only: uplo 'L' updates the elements with column <= row, 'U' those
+ * with column >= row.  op(A) is N x K and op(B) is K x N (layouts as for
+ * ooc_dgemm with M = N).  Elements of the other triangle keep their values:
+ * blocks of C that hold no updated element are never copied, and blocks that
+ * straddle the diagonal are copied to the device and back whole (so the host
+ * memory of the other triangle must not change during the call).  beta == 0
+ * never reads the updated triangle.  opts->form: FP64 (default) or Ozaki.
+ * stats->tflops counts N (N + 1) K flops.
+ */
+int ooc_dgemmt(char uplo, char transA, char transB, int64_t N, int64_t K, double alpha,
+               const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
+               double* C, int64_t ldc, size_t device_budget_bytes, const ooc_opts* opts,
+               ooc_stats* stats);
+
+/*
+ * SYRK: C = alpha * op(A) * op(A)^T + beta * C on the uplo triangle of the
+ * N x N matrix C; trans 'N': A is stored N x K (lda >= K) and the update is
+ * A A^T; 'T': A is stored K x N (lda >= N) and the update is A^T A.  Same
+ * rules as ooc_dgemmt.  ooc_ssyrk takes FP32 operands and runs the BF16x3
+ * form (alpha and beta applied in FP64 before rounding to FP32).
+ */
+int ooc_dsyrk(char uplo, char trans, int64_t N, int64_t K, double alpha, const double* A,
+              int64_t lda, double beta, double* C, int64_t ldc, size_t device_budget_bytes,
+              const ooc_opts* opts, ooc_stats* stats);
+int ooc_ssyrk(char uplo, char trans, int64_t N, int64_t K, float alpha, const float* A,
+              int64_t lda, float beta, float* C, int64_t ldc, size_t device_budget_bytes,
+              const ooc_opts* opts, ooc_stats* stats);
+
+/*
+ * TRSM: solve op(A) X = alpha B (side 'L', A of order M) or X op(A) = alpha B
+ * (side 'R', A of order N) for X, which overwrites the M x N matrix B.  A is
+ * triangular: uplo 'L' or 'U' names the stored triangle (the other one is not
+ * read); transA 'N' or 'T' gives op(A); diag 'U' takes the diagonal as ones
+ * (not read), 'N' reads it.  Left-looking over panels of X: each panel is
+ * updated with one out-of-core GEMM over the panels already solved (opts->form
+ * FP64 or Ozaki) and then solved in device memory.  alpha == 0 sets B to zero
+ * without reading it.  No check for a singular A: a zero diagonal element
+ * gives infinities or NaN, as in BLAS.  The call allocates one device arena of
+ * device_budget_bytes (opts->workspace must be NULL).  stats: seconds, tflops
+ * (M^2 N flops for side 'L', M N^2 for 'R'), bytes moved, GEMM calls in steps.
+ */
+int ooc_dtrsm(char side, char uplo, char transA, char diag, int64_t M, int64_t N, double alpha,
+              const double* A, int64_t lda, double* B, int64_t ldb, size_t device_budget_bytes,
+              const ooc_opts* opts, ooc_stats* stats);
+
+/*
+ * POTRF: Cholesky factorisation of the symmetric positive definite N x N
+ * matrix A in place: uplo 'L' gives A = L L^T with L in the lower triangle,
+ * 'U' gives A = U^T U with U in the upper triangle; the other triangle is
+ * neither used nor changed.  Left-looking over panels: each panel is updated
+ * with one out-of-core GEMMT (opts->form FP64 or Ozaki) and factored in device
+ * memory.  *info is 0 on success, or j + 1 when the leading minor of order
+ * j + 1 is not positive definite (the status is still OOC_OK; panels before
+ * the one holding column j are final, the rest of A is unspecified).  Same
+ * arena rule as ooc_dtrsm; stats->tflops counts N^3 / 3 flops.
+ */
+int ooc_dpotrf(char uplo, int64_t N, double* A, int64_t lda, size_t device_budget_bytes,
+               const ooc_opts* opts, ooc_stats* stats, int64_t* info);
+
 /*
  * Plan only (host, no device needed): the block/chunk/buffer plan the call
  * with these arguments would use.  elem_bytes is 8 for ooc_dgemm, 4 for
@@ -232,6 +298,16 @@ typedef struct {
 int ooc_schedule(int64_t M, int64_t N, int64_t K, int32_t elem_bytes, int32_t beta_nonzero,
                  size_t device_budget_bytes, const ooc_opts* opts, ooc_sched_op* out,
                  int64_t capacity, int64_t* count);
+
+/*
+ * Export the schedule of ooc_dgemmt / ooc_dsyrk (elem_bytes 8) or ooc_ssyrk
+ * (4) for an N x N C and inner dimension K, as ooc_schedule does; plan
+ * (nullable) receives the plan fields as ooc_plan fills them, with blocks and
+ * steps counting the updated blocks only.
+ */
+int ooc_schedule_gemmt(char uplo, int64_t N, int64_t K, int32_t elem_bytes, int32_t beta_nonzero,
+                       size_t device_budget_bytes, const ooc_opts* opts, ooc_stats* plan,
+                       ooc_sched_op* out, int64_t capacity, int64_t* count);
 
 /* ---- plan search: candidates, autotuner, learned cost model ------------ */
 /* The paper has no plan search beyond its partitioner (Section IV); these

@@ -119,12 +119,20 @@ def load(path=None):
     lib.ooc_plan.argtypes = [i64, i64, i64, i32, i32, sz, po, ps]
     lib.ooc_schedule.argtypes = [i64, i64, i64, i32, i32, sz, po, ctypes.POINTER(ooc_sched_op), i64,
                                  ctypes.POINTER(i64)]
+    lib.ooc_dgemmt.argtypes = [ch, ch, ch, i64, i64, dbl, vp, i64, vp, i64, dbl, vp, i64, sz, po, ps]
+    lib.ooc_dsyrk.argtypes = [ch, ch, i64, i64, dbl, vp, i64, dbl, vp, i64, sz, po, ps]
+    lib.ooc_ssyrk.argtypes = [ch, ch, i64, i64, flt, vp, i64, flt, vp, i64, sz, po, ps]
+    lib.ooc_schedule_gemmt.argtypes = [ch, i64, i64, i32, i32, sz, po, ps, ctypes.POINTER(ooc_sched_op), i64,
+                                       ctypes.POINTER(i64)]
+    lib.ooc_dtrsm.argtypes = [ch, ch, ch, ch, i64, i64, dbl, vp, i64, vp, i64, sz, po, ps]
+    lib.ooc_dpotrf.argtypes = [ch, i64, vp, i64, sz, po, ps, ctypes.POINTER(i64)]
     lib.ooc_query_device.argtypes = [ctypes.POINTER(sz), ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
     lib.ooc_strerror.argtypes = [ctypes.c_int]
     lib.ooc_strerror.restype = ctypes.c_char_p
     lib.ooc_last_error.argtypes = []
     lib.ooc_last_error.restype = ctypes.c_char_p
-    for f in ("ooc_dgemm", "ooc_sgemm", "ooc_dgemm_device", "ooc_plan", "ooc_schedule", "ooc_query_device"):
+    for f in ("ooc_dgemm", "ooc_sgemm", "ooc_dgemm_device", "ooc_plan", "ooc_schedule", "ooc_query_device",
+              "ooc_dgemmt", "ooc_dsyrk", "ooc_ssyrk", "ooc_schedule_gemmt", "ooc_dtrsm", "ooc_dpotrf"):
         getattr(lib, f).restype = ctypes.c_int
     if path is None:
         _lib = lib
@@ -186,6 +194,41 @@ def ooc_sgemm(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, budg
                          ctypes.byref(stats) if stats is not None else None)
 
 
+def _ref(x):
+    return ctypes.byref(x) if x is not None else None
+
+
+def ooc_dgemmt(uplo, transA, transB, N, K, alpha, A, lda, B, ldb, beta, C, ldc, budget, opts=None, stats=None):
+    """C ABI ooc_dgemmt (triangular part of C = alpha op(A) op(B) + beta C); returns the status code."""
+    return load().ooc_dgemmt(uplo.encode(), transA.encode(), transB.encode(), N, K, alpha, _ptr(A), lda, _ptr(B),
+                             ldb, beta, _ptr(C), ldc, budget, _ref(opts), _ref(stats))
+
+
+def ooc_dsyrk(uplo, trans, N, K, alpha, A, lda, beta, C, ldc, budget, opts=None, stats=None):
+    """C ABI ooc_dsyrk; returns the status code."""
+    return load().ooc_dsyrk(uplo.encode(), trans.encode(), N, K, alpha, _ptr(A), lda, beta, _ptr(C), ldc, budget,
+                            _ref(opts), _ref(stats))
+
+
+def ooc_ssyrk(uplo, trans, N, K, alpha, A, lda, beta, C, ldc, budget, opts=None, stats=None):
+    """C ABI ooc_ssyrk (BF16x3 form); returns the status code."""
+    return load().ooc_ssyrk(uplo.encode(), trans.encode(), N, K, alpha, _ptr(A), lda, beta, _ptr(C), ldc, budget,
+                            _ref(opts), _ref(stats))
+
+
+def ooc_dtrsm(side, uplo, transA, diag, M, N, alpha, A, lda, B, ldb, budget, opts=None, stats=None):
+    """C ABI ooc_dtrsm (X overwrites B); returns the status code."""
+    return load().ooc_dtrsm(side.encode(), uplo.encode(), transA.encode(), diag.encode(), M, N, alpha, _ptr(A), lda,
+                            _ptr(B), ldb, budget, _ref(opts), _ref(stats))
+
+
+def ooc_dpotrf(uplo, N, A, lda, budget, opts=None, stats=None):
+    """C ABI ooc_dpotrf; returns (status code, info)."""
+    info = ctypes.c_int64(0)
+    rc = load().ooc_dpotrf(uplo.encode(), N, _ptr(A), lda, budget, _ref(opts), _ref(stats), ctypes.byref(info))
+    return rc, info.value
+
+
 def ooc_dgemm_batched(descs, budget, opts=None, stats=None):
     """C ABI ooc_dgemm_batched on a list of ooc_gemm_desc; returns the status code."""
     lib = load()
@@ -245,14 +288,29 @@ def ooc_plan(M, N, K, elem_bytes, beta_nonzero, budget, opts=None):
 def ooc_schedule(M, N, K, elem_bytes, beta_nonzero, budget, opts=None):
     """C ABI ooc_schedule; returns the issued operations as a list of dicts."""
     lib = load()
+    o = _ref(opts)
+    return _export(lambda buf, cap, n: lib.ooc_schedule(M, N, K, elem_bytes, int(bool(beta_nonzero)), budget, o,
+                                                        buf, cap, n), "ooc_schedule")
+
+
+def ooc_schedule_gemmt(uplo, N, K, elem_bytes, beta_nonzero, budget, opts=None):
+    """C ABI ooc_schedule_gemmt; returns (plan dict, list of operation dicts)."""
+    lib = load()
+    o = _ref(opts)
+    st = ooc_stats()
+    ops = _export(lambda buf, cap, n: lib.ooc_schedule_gemmt(uplo.encode(), N, K, elem_bytes,
+                                                             int(bool(beta_nonzero)), budget, o, ctypes.byref(st),
+                                                             buf, cap, n), "ooc_schedule_gemmt")
+    return st.as_dict(), ops
+
+
+def _export(call, name):
     n = ctypes.c_int64(0)
-    o = ctypes.byref(opts) if opts is not None else None
-    rc = lib.ooc_schedule(M, N, K, elem_bytes, int(bool(beta_nonzero)), budget, o, None, 0, ctypes.byref(n))
+    rc = call(None, 0, ctypes.byref(n))
     if rc not in (OOC_OK, OOC_ERR_CAPACITY):
-        _check(rc, "ooc_schedule")
+        _check(rc, name)
     buf = (ooc_sched_op * max(1, n.value))()
-    _check(lib.ooc_schedule(M, N, K, elem_bytes, int(bool(beta_nonzero)), budget, o, buf, n.value,
-                            ctypes.byref(n)), "ooc_schedule")
+    _check(call(buf, n.value, ctypes.byref(n)), name)
     out = []
     for k in range(n.value):
         e = buf[k]

@@ -1,0 +1,555 @@
+// Out-of-core triangular solve (TRSM) and Cholesky factorisation (POTRF)
+// built on the out-of-core GEMM -- the step Section VII of the paper names
+// after its DGEMM: the rest of level-3 BLAS and the factorisations that use
+// the out-of-core DGEMM as their building block.
+//
+// Both drivers are left-looking over panels of the solution / factor:
+//   1. the panel is brought up to date with one out-of-core GEMM (GEMMT with a
+//      triangle mask for Cholesky) over everything already solved, streamed
+//      from host memory by the Section IV pipeline (ooc_api.cu);
+//   2. the panel is solved / factored in device memory by a recursive
+//      blocked algorithm: triangular blocks of at most 64 by the substitution
+//      and Cholesky kernels below, everything else by the FP64 tile kernel.
+// So nearly all flops run in the pipelined GEMM, in the caller's form (FP64
+// tiles, or the FP64-accurate Ozaki tensor-core form).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "ooc_internal.hpp"
+
+namespace ooc {
+
+namespace {
+
+constexpr int kSmall = 64;     // order of the triangular blocks the small kernels take
+constexpr int kVecs = 128;     // right-hand sides per CTA of the substitution kernel
+
+// Solve Tm x = alpha p for nvec vectors p of n <= 64 elements, where
+// Tm[r][c] = T[c][r] if t_trans else T[r][c], lower or upper triangular (only
+// that triangle of the stored T is read), unit diagonal (not read) or not.
+// Element e of vector v lives at P[e * es + v * vs].
+__global__ void __launch_bounds__(kVecs) trsm_small_kernel(const double* __restrict__ T, int64_t ldt, int n,
+                                                           int t_trans, int lower, int unit, double* P, int64_t es,
+                                                           int64_t vs, int64_t nvec, double alpha)
+{
+    // dynamic shared memory (above the 48 KB static limit): the block, then the vectors
+    extern __shared__ double smem_f64[];
+    double (*Ts)[kSmall + 1] = reinterpret_cast<double (*)[kSmall + 1]>(smem_f64);
+    double (*Xs)[kSmall + 1] = reinterpret_cast<double (*)[kSmall + 1]>(smem_f64 + kSmall * (kSmall + 1));
+    const int tid = threadIdx.x;
+    const int64_t v0 = (int64_t)blockIdx.x * kVecs;
+    for (int idx = tid; idx < n * n; idx += blockDim.x) {
+        const int r = idx / n, c = idx % n;
+        double t = 0.0;
+        if (r == c) t = unit ? 1.0 : T[(int64_t)r * ldt + c];
+        else if (lower ? c < r : c > r) t = t_trans ? T[(int64_t)c * ldt + r] : T[(int64_t)r * ldt + c];
+        Ts[r][c] = t;
+    }
+    // stage the vectors, the unit-stride index fastest for coalescing
+    const bool v_fast = vs == 1;
+    for (int idx = tid; idx < n * kVecs; idx += blockDim.x) {
+        const int e = v_fast ? idx / kVecs : idx % n;
+        const int v = v_fast ? idx % kVecs : idx / n;
+        if (v0 + v < nvec) Xs[v][e] = P[(int64_t)e * es + (v0 + v) * vs];
+    }
+    __syncthreads();
+    if (v0 + tid < nvec) {
+        double* x = Xs[tid];
+        for (int q = 0; q < n; ++q) {
+            const int r = lower ? q : n - 1 - q;
+            double s = alpha * x[r];
+            if (lower)
+                for (int c = 0; c < r; ++c) s -= Ts[r][c] * x[c];
+            else
+                for (int c = r + 1; c < n; ++c) s -= Ts[r][c] * x[c];
+            x[r] = unit ? s : s / Ts[r][r];
+        }
+    }
+    __syncthreads();
+    for (int idx = tid; idx < n * kVecs; idx += blockDim.x) {
+        const int e = v_fast ? idx / kVecs : idx % n;
+        const int v = v_fast ? idx % kVecs : idx / n;
+        if (v0 + v < nvec) P[(int64_t)e * es + (v0 + v) * vs] = Xs[v][e];
+    }
+}
+
+// Cholesky of one n x n block (n <= 64) in place: the lower triangle of T
+// becomes L with L L^T = T (upper != 0: the upper triangle becomes U = L^T
+// with U^T U = T).  Only that triangle is read and written.  A pivot that is
+// not positive stops the block and records gofs + its column + 1 in *info
+// (first failure wins).
+__global__ void __launch_bounds__(256) potrf_small_kernel(double* T, int64_t ldt, int n, int upper, int64_t gofs,
+                                                          unsigned long long* info)
+{
+    __shared__ double S[kSmall][kSmall + 1];
+    __shared__ int fail;
+    const int tid = threadIdx.x;
+    for (int idx = tid; idx < n * n; idx += blockDim.x) {
+        const int r = idx / n, c = idx % n;
+        if (c <= r) S[r][c] = upper ? T[(int64_t)c * ldt + r] : T[(int64_t)r * ldt + c];
+    }
+    if (tid == 0) fail = 0;
+    __syncthreads();
+    for (int j = 0; j < n; ++j) {
+        if (tid == 0) {
+            const double d = S[j][j];
+            if (d > 0.0) S[j][j] = sqrt(d);
+            else fail = j + 1;
+        }
+        __syncthreads();
+        if (fail) break;
+        for (int i = j + 1 + tid; i < n; i += blockDim.x) S[i][j] = S[i][j] / S[j][j];
+        __syncthreads();
+        const int m = n - j - 1;
+        for (int idx = tid; idx < m * m; idx += blockDim.x) {
+            const int i = j + 1 + idx / m, k = j + 1 + idx % m;
+            if (k <= i) S[i][k] -= S[i][j] * S[k][j];
+        }
+        __syncthreads();
+    }
+    if (tid == 0 && fail) atomicCAS(info, 0ull, (unsigned long long)(gofs + fail));
+    for (int idx = tid; idx < n * n; idx += blockDim.x) {
+        const int r = idx / n, c = idx % n;
+        if (c <= r) {
+            if (upper) T[(int64_t)c * ldt + r] = S[r][c];
+            else T[(int64_t)r * ldt + c] = S[r][c];
+        }
+    }
+}
+
+__global__ void scale_kernel(double* P, int64_t ld, int64_t rows, int64_t cols, double alpha)
+{
+    const int64_t n = rows * cols;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / cols, c = i % cols;
+        P[r * ld + c] *= alpha;
+    }
+}
+
+constexpr size_t kTrsmSmem = (size_t)(kSmall + kVecs) * (kSmall + 1) * sizeof(double);
+
+int check_launch(const char* what, std::string& why)
+{
+    const cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) return OOC_OK;
+    why = std::string(what) + ": " + cudaGetErrorString(e);
+    return OOC_ERR_CUDA;
+}
+
+// Device state of one driver call.
+struct Dev {
+    cudaStream_t st = nullptr;
+    int* err = nullptr;                  // error word of the tile kernels' bounded waits
+    unsigned long long* info = nullptr;  // first failed Cholesky pivot (global column + 1)
+    int64_t launches = 0;
+};
+
+// Split n > 64 at a multiple of 64 near its middle (keeps sub-blocks 16-byte aligned for TMA).
+int64_t split_point(int64_t n) { return std::max<int64_t>(kSmall, (n / 2) / kSmall * kSmall); }
+
+// The stored position of the sub-block of op(T) at (r0, c0), as a tile-kernel
+// operand: as an A operand it is "rows x K" stored (a_kmajor) unless T is
+// transposed; as a B operand it is "cols x K" stored (b_kmajor) iff T is.
+const double* opT_block(const double* T, int64_t ldt, bool t_trans, int64_t r0, int64_t c0)
+{
+    return t_trans ? T + c0 * ldt + r0 : T + r0 * ldt + c0;
+}
+
+// In device memory: solve op(T) X = P (left) or X op(T) = P (right) in place
+// in P, op(T) of order n lower (op_lower) or upper triangular; P is n x nv
+// (left) or nv x n (right), row-major with leading dimension ldp.
+int incore_trsm(bool left, bool op_lower, const double* T, int64_t ldt, bool t_trans, bool unit, int64_t n,
+                double* P, int64_t ldp, int64_t nv, Dev& d, std::string& why)
+{
+    if (n <= 0 || nv <= 0) return OOC_OK;
+    if (n <= kSmall) {
+        // the substitution kernel solves Tm x = p: Tm = op(T) (left) or op(T)^T (right)
+        const bool tm_lower = left ? op_lower : !op_lower;
+        const bool tm_trans = left ? t_trans : !t_trans;
+        const int64_t es = left ? ldp : 1, vs = left ? 1 : ldp;
+        const int64_t grid = (nv + kVecs - 1) / kVecs;
+        static const cudaError_t attr = cudaFuncSetAttribute(
+            trsm_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTrsmSmem);
+        if (attr != cudaSuccess) {
+            why = std::string("trsm_small_kernel shared memory: ") + cudaGetErrorString(attr);
+            return OOC_ERR_CUDA;
+        }
+        trsm_small_kernel<<<(unsigned)grid, kVecs, kTrsmSmem, d.st>>>(T, ldt, (int)n, tm_trans ? 1 : 0, tm_lower ? 1 : 0,
+                                                               unit ? 1 : 0, P, es, vs, nv, 1.0);
+        ++d.launches;
+        return check_launch("trsm_small_kernel", why);
+    }
+    const int64_t n1 = split_point(n), n2 = n - n1;
+    const double* T11 = T;
+    const double* T22 = T + n1 * ldt + n1;
+    int rc;
+    auto gemm = [&](bool a_k, bool b_k, int64_t M, int64_t N, int64_t K, const double* A, int64_t lda,
+                    const double* B, int64_t ldb, double* C) {
+        ++d.launches;
+        return launch_fp64_tile(a_k, b_k, M, N, K, -1.0, A, lda, B, ldb, 1.0, true, C, ldp, d.err, d.st, why);
+    };
+    if (left) {
+        double* P1 = P;
+        double* P2 = P + n1 * ldp;
+        if (op_lower) {  // X1 = T11 \ P1;  P2 -= T21 X1;  X2 = T22 \ P2
+            if ((rc = incore_trsm(left, op_lower, T11, ldt, t_trans, unit, n1, P1, ldp, nv, d, why))) return rc;
+            if ((rc = gemm(!t_trans, false, n2, nv, n1, opT_block(T, ldt, t_trans, n1, 0), ldt, P1, ldp, P2)))
+                return rc;
+            return incore_trsm(left, op_lower, T22, ldt, t_trans, unit, n2, P2, ldp, nv, d, why);
+        }
+        // upper: X2 = T22 \ P2;  P1 -= T12 X2;  X1 = T11 \ P1
+        if ((rc = incore_trsm(left, op_lower, T22, ldt, t_trans, unit, n2, P2, ldp, nv, d, why))) return rc;
+        if ((rc = gemm(!t_trans, false, n1, nv, n2, opT_block(T, ldt, t_trans, 0, n1), ldt, P2, ldp, P1))) return rc;
+        return incore_trsm(left, op_lower, T11, ldt, t_trans, unit, n1, P1, ldp, nv, d, why);
+    }
+    double* P1 = P;        // columns [0, n1)
+    double* P2 = P + n1;   // columns [n1, n)
+    if (op_lower) {  // X2 = P2 / T22;  P1 -= X2 T21;  X1 = P1 / T11
+        if ((rc = incore_trsm(left, op_lower, T22, ldt, t_trans, unit, n2, P2, ldp, nv, d, why))) return rc;
+        if ((rc = gemm(true, t_trans, nv, n1, n2, P2, ldp, opT_block(T, ldt, t_trans, n1, 0), ldt, P1))) return rc;
+        return incore_trsm(left, op_lower, T11, ldt, t_trans, unit, n1, P1, ldp, nv, d, why);
+    }
+    // upper: X1 = P1 / T11;  P2 -= X1 T12;  X2 = P2 / T22
+    if ((rc = incore_trsm(left, op_lower, T11, ldt, t_trans, unit, n1, P1, ldp, nv, d, why))) return rc;
+    if ((rc = gemm(true, t_trans, nv, n2, n1, P1, ldp, opT_block(T, ldt, t_trans, 0, n1), ldt, P2))) return rc;
+    return incore_trsm(left, op_lower, T22, ldt, t_trans, unit, n2, P2, ldp, nv, d, why);
+}
+
+// In device memory: Cholesky of the n x n block T in place (lower: L L^T,
+// upper: U^T U); gofs is the block's first global column (for info).
+int incore_potrf(bool upper, double* T, int64_t ldt, int64_t n, int64_t gofs, Dev& d, std::string& why)
+{
+    if (n <= kSmall) {
+        potrf_small_kernel<<<1, 256, 0, d.st>>>(T, ldt, (int)n, upper ? 1 : 0, gofs, d.info);
+        ++d.launches;
+        return check_launch("potrf_small_kernel", why);
+    }
+    const int64_t n1 = split_point(n), n2 = n - n1;
+    double* T22 = T + n1 * ldt + n1;
+    int rc;
+    if ((rc = incore_potrf(upper, T, ldt, n1, gofs, d, why))) return rc;
+    if (!upper) {
+        // L21 = T21 L11^{-T} (right solve with op = transpose of the stored lower L11, an upper op)
+        double* T21 = T + n1 * ldt;
+        if ((rc = incore_trsm(false, false, T, ldt, true, false, n1, T21, ldt, n2, d, why))) return rc;
+        // T22 -= L21 L21^T on the lower triangle
+        ++d.launches;
+        if ((rc = launch_fp64_tile(true, true, n2, n2, n1, -1.0, T21, ldt, T21, ldt, 1.0, true, T22, ldt, d.err, d.st,
+                                   why, 1, 0)))
+            return rc;
+    } else {
+        // U12 = U11^{-T} T12 (left solve with op = transpose of the stored upper U11, a lower op)
+        double* T12 = T + n1;
+        if ((rc = incore_trsm(true, true, T, ldt, true, false, n1, T12, ldt, n2, d, why))) return rc;
+        // T22 -= U12^T U12 on the upper triangle
+        ++d.launches;
+        if ((rc = launch_fp64_tile(false, false, n2, n2, n1, -1.0, T12, ldt, T12, ldt, 1.0, true, T22, ldt, d.err,
+                                   d.st, why, 2, 0)))
+            return rc;
+    }
+    return incore_potrf(upper, T22, ldt, n2, gofs + n1, d, why);
+}
+
+int64_t round_up64(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+bool is_l(char c) { return c == 'L' || c == 'l'; }
+bool is_r(char c) { return c == 'R' || c == 'r'; }
+bool is_u(char c) { return c == 'U' || c == 'u'; }
+bool is_n(char c) { return c == 'N' || c == 'n'; }
+bool is_t(char c) { return c == 'T' || c == 't'; }
+
+int fail(int code, const std::string& msg)
+{
+    set_error(msg);
+    return code;
+}
+
+// One driver call: a device arena of the budget (its first 256 bytes hold the
+// error word and the pivot word), one stream, the running statistics.
+struct Driver {
+    char* arena = nullptr;
+    size_t bytes = 0;
+    Dev d;
+    double h2d = 0, d2h = 0, kernel_s = 0;
+    int64_t steps = 0, launches = 0;
+    ooc_opts gemm_opts;
+    std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+
+    ~Driver()
+    {
+        if (d.st) {
+            cudaStreamSynchronize(d.st);
+            cudaStreamDestroy(d.st);
+        }
+        if (arena) cudaFree(arena);
+        cudaGetLastError();
+    }
+
+    int init(size_t budget, const ooc_opts* opts, std::string& why)
+    {
+        std::memset(&gemm_opts, 0, sizeof(gemm_opts));
+        if (opts) gemm_opts = *opts;
+        if (gemm_opts.workspace) {
+            why = "the TRSM / Cholesky drivers allocate their own arena (opts->workspace must be NULL)";
+            return OOC_ERR_INVALID_ARG;
+        }
+        bytes = budget;
+        if (cudaMalloc(&arena, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            arena = nullptr;
+            why = "device arena of " + std::to_string(bytes) + " bytes";
+            return OOC_ERR_ALLOC;
+        }
+        if (cudaStreamCreateWithFlags(&d.st, cudaStreamNonBlocking) != cudaSuccess) {
+            why = "stream creation failed";
+            return OOC_ERR_CUDA;
+        }
+        d.err = reinterpret_cast<int*>(arena);
+        d.info = reinterpret_cast<unsigned long long*>(arena + 8);
+        if (cudaMemsetAsync(arena, 0, 256, d.st) != cudaSuccess) return OOC_ERR_CUDA;
+        gemm_opts.workspace = arena + 256;
+        gemm_opts.workspace_bytes = bytes - 256;
+        return OOC_OK;
+    }
+
+    // one out-of-core GEMM over host operands, in the arena
+    int gemm(char ta, char tb, int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t lda,
+             const double* B, int64_t ldb, double beta, double* C, int64_t ldc, int tri)
+    {
+        if (cudaStreamSynchronize(d.st) != cudaSuccess) return fail(OOC_ERR_CUDA, "stream synchronise failed");
+        ooc_stats st;
+        const int rc = run_gemm_host(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, 8, bytes - 256,
+                                     &gemm_opts, &st, tri, 0);
+        if (rc) return rc;
+        h2d += st.h2d_bytes;
+        d2h += st.d2h_bytes;
+        kernel_s += st.kernel_seconds;
+        launches += st.kernel_launches;
+        ++steps;
+        return OOC_OK;
+    }
+
+    int copy_in(double* dst, int64_t ldd, const double* src, int64_t lds, int64_t rows, int64_t cols)
+    {
+        if (rows <= 0 || cols <= 0) return OOC_OK;
+        if (cudaMemcpy2DAsync(dst, ldd * 8, src, lds * 8, cols * 8, rows, cudaMemcpyHostToDevice, d.st) !=
+            cudaSuccess)
+            return fail(OOC_ERR_CUDA, "panel copy to the device failed");
+        h2d += (double)rows * cols * 8;
+        return OOC_OK;
+    }
+
+    int copy_out(double* dst, int64_t ldd, const double* src, int64_t lds, int64_t rows, int64_t cols)
+    {
+        if (rows <= 0 || cols <= 0) return OOC_OK;
+        if (cudaMemcpy2DAsync(dst, ldd * 8, src, lds * 8, cols * 8, rows, cudaMemcpyDeviceToHost, d.st) !=
+            cudaSuccess)
+            return fail(OOC_ERR_CUDA, "panel copy to the host failed");
+        d2h += (double)rows * cols * 8;
+        return OOC_OK;
+    }
+
+    // wait for the stream and turn a device-side error word into a status
+    int drain()
+    {
+        if (cudaStreamSynchronize(d.st) != cudaSuccess)
+            return fail(OOC_ERR_CUDA, std::string("panel stream: ") + cudaGetErrorString(cudaGetLastError()));
+        int herr = 0;
+        if (cudaMemcpy(&herr, d.err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return fail(OOC_ERR_CUDA, "error word read failed");
+        if (herr) return fail(OOC_ERR_TIMEOUT, "a device-side wait gave up (status " + std::to_string(herr) + ")");
+        return OOC_OK;
+    }
+
+    void finish(ooc_stats* stats, double flops)
+    {
+        if (!stats) return;
+        std::memset(stats, 0, sizeof(*stats));
+        stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        stats->device_seconds = stats->seconds;
+        stats->kernel_seconds = kernel_s;
+        stats->tflops = stats->seconds > 0 ? flops / stats->seconds / 1e12 : 0.0;
+        stats->h2d_bytes = h2d;
+        stats->d2h_bytes = d2h;
+        stats->form = gemm_opts.form;
+        stats->steps = steps;
+        stats->device_bytes = (int64_t)bytes;
+        stats->kernel_launches = launches + d.launches;
+    }
+};
+
+// Panel order for a budget: t x t triangular block plus at least 64 vectors of t.
+int64_t panel_order(int64_t n, size_t budget)
+{
+    const double usable = (double)budget * 0.45;  // the block and one chunk of right-hand sides
+    int64_t t = (int64_t)(std::sqrt(usable / 8.0)) / kSmall * kSmall;
+    t = std::min<int64_t>(t, 1024);
+    if (t < kSmall) t = kSmall;
+    return std::min<int64_t>(t, n);
+}
+
+}  // namespace
+
+}  // namespace ooc
+
+using namespace ooc;
+
+int ooc_dtrsm(char side, char uplo, char transA, char diag, int64_t M, int64_t N, double alpha, const double* A,
+              int64_t lda, double* B, int64_t ldb, size_t device_budget_bytes, const ooc_opts* opts,
+              ooc_stats* stats)
+{
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    if (!(is_l(side) || is_r(side)) || !(is_l(uplo) || is_u(uplo)) || !(is_n(transA) || is_t(transA)) ||
+        !(is_n(diag) || is_u(diag)))
+        return fail(OOC_ERR_INVALID_ARG, "side, uplo, transA or diag out of range");
+    if (M < 0 || N < 0) return fail(OOC_ERR_INVALID_ARG, "negative dimension");
+    const bool left = is_l(side);
+    const int64_t n = left ? M : N;  // order of A
+    if (lda < std::max<int64_t>(1, n) || ldb < std::max<int64_t>(1, N))
+        return fail(OOC_ERR_INVALID_ARG, "leading dimension below the row width");
+    if (M == 0 || N == 0) return OOC_OK;
+    if (!A || !B) return fail(OOC_ERR_INVALID_ARG, "null operand pointer");
+    std::string why;
+    int rc = device_check(why);
+    if (rc) return fail(rc, why);
+    if (!host_range_pinned(A, n, n, lda, 8) || !host_range_pinned(B, M, N, ldb, 8))
+        return fail(OOC_ERR_NOT_PINNED, "host operands must be page-locked (cudaHostAlloc / cudaHostRegister)");
+    const int64_t t = panel_order(n, device_budget_bytes);
+    const int64_t ldt = round_up64(t, 16);
+    if ((size_t)(t * ldt * 8 + 256 + 64 * ldt * 8 + 4096) > device_budget_bytes)
+        return fail(OOC_ERR_BUDGET, "budget below one 64 x 64 triangular block and its right-hand sides");
+    Driver dr;
+    if ((rc = dr.init(device_budget_bytes, opts, why))) return fail(rc, why);
+    if (alpha == 0.0) {
+        // X = 0 without reading B (the BLAS rule for alpha == 0)
+        for (int64_t r = 0; r < M; ++r) std::memset(B + r * ldb, 0, (size_t)N * 8);
+        dr.finish(stats, 0.0);
+        return OOC_OK;
+    }
+    const bool trans = is_t(transA), unit = is_u(diag);
+    const bool op_lower = is_l(uplo) != trans;
+    const bool forward = left ? op_lower : !op_lower;  // the coupled unknowns come first
+    double* dT = reinterpret_cast<double*>(dr.arena + 256);
+    double* dP = dT + t * ldt;
+    const size_t p_bytes = dr.bytes - 256 - (size_t)(t * ldt * 8);
+    const int64_t np = (n + t - 1) / t;
+    for (int64_t q = 0; q < np; ++q) {
+        const int64_t k = forward ? q : np - 1 - q;
+        const int64_t r0 = k * t, tk = std::min(t, n - r0);
+        // the unknowns already solved: [0, r0) going forward, [r0 + tk, n) going backward
+        const int64_t s0 = forward ? 0 : r0 + tk, ks = forward ? r0 : n - (r0 + tk);
+        if (ks > 0) {
+            // panel -= op(A)[panel, solved] X[solved] (side L), X[:, solved] op(A)[solved, panel] (side R);
+            // beta = alpha applies the scale of the right-hand side once, here
+            if (left)
+                rc = dr.gemm(trans ? 'T' : 'N', 'N', tk, N, ks, -1.0, trans ? A + s0 * lda + r0 : A + r0 * lda + s0,
+                             lda, B + s0 * ldb, ldb, alpha, B + r0 * ldb, ldb, 0);
+            else
+                rc = dr.gemm('N', trans ? 'T' : 'N', M, tk, ks, -1.0, B + s0, ldb,
+                             trans ? A + r0 * lda + s0 : A + s0 * lda + r0, lda, alpha, B + r0, ldb, 0);
+            if (rc) return rc;
+        }
+        const double scale = ks > 0 ? 1.0 : alpha;
+        // the triangular block A_kk (as stored) and the panel in chunks of right-hand sides
+        if ((rc = dr.copy_in(dT, ldt, A + r0 * lda + r0, lda, tk, tk))) return rc;
+        const int64_t lp = round_up64(left ? 1 : tk, 16);  // leading dimension of a right-side chunk
+        int64_t chunk;
+        if (left) chunk = std::max<int64_t>(kSmall, (int64_t)(p_bytes / (8 * (size_t)tk)) / 16 * 16);
+        else chunk = std::max<int64_t>(kSmall, (int64_t)(p_bytes / (8 * (size_t)lp)));
+        const int64_t nv_total = left ? N : M;
+        for (int64_t v0 = 0; v0 < nv_total; v0 += chunk) {
+            const int64_t nv = std::min(chunk, nv_total - v0);
+            const int64_t ldp = left ? round_up64(nv, 16) : lp;
+            double* hP = left ? B + r0 * ldb + v0 : B + v0 * ldb + r0;
+            const int64_t rows = left ? tk : nv, cols = left ? nv : tk;
+            if ((rc = dr.copy_in(dP, ldp, hP, ldb, rows, cols))) return rc;
+            if (scale != 1.0) {
+                scale_kernel<<<1024, 256, 0, dr.d.st>>>(dP, ldp, rows, cols, scale);
+                ++dr.d.launches;
+                if ((rc = check_launch("scale_kernel", why))) return fail(rc, why);
+            }
+            if ((rc = incore_trsm(left, op_lower, dT, ldt, trans, unit, tk, dP, ldp, nv, dr.d, why)))
+                return fail(rc, why);
+            if ((rc = dr.copy_out(hP, ldb, dP, ldp, rows, cols))) return rc;
+            if ((rc = dr.drain())) return rc;
+        }
+    }
+    dr.finish(stats, left ? (double)M * M * N : (double)M * N * N);
+    return OOC_OK;
+}
+
+int ooc_dpotrf(char uplo, int64_t N, double* A, int64_t lda, size_t device_budget_bytes, const ooc_opts* opts,
+               ooc_stats* stats, int64_t* info)
+{
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    if (info) *info = 0;
+    if (!(is_l(uplo) || is_u(uplo))) return fail(OOC_ERR_INVALID_ARG, "uplo must be 'L' or 'U'");
+    if (N < 0 || lda < std::max<int64_t>(1, N)) return fail(OOC_ERR_INVALID_ARG, "bad order or leading dimension");
+    if (N == 0) return OOC_OK;
+    if (!A || !info) return fail(OOC_ERR_INVALID_ARG, "null matrix or info pointer");
+    std::string why;
+    int rc = device_check(why);
+    if (rc) return fail(rc, why);
+    if (!host_range_pinned(A, N, N, lda, 8))
+        return fail(OOC_ERR_NOT_PINNED, "host operands must be page-locked (cudaHostAlloc / cudaHostRegister)");
+    const int64_t t = panel_order(N, device_budget_bytes);
+    const int64_t ldt = round_up64(t, 16);
+    if ((size_t)(t * ldt * 8 + 256 + 64 * ldt * 8 + 4096) > device_budget_bytes)
+        return fail(OOC_ERR_BUDGET, "budget below one 64 x 64 diagonal block and its panel rows");
+    Driver dr;
+    if ((rc = dr.init(device_budget_bytes, opts, why))) return fail(rc, why);
+    const bool upper = is_u(uplo);
+    double* dT = reinterpret_cast<double*>(dr.arena + 256);
+    double* dP = dT + t * ldt;
+    const size_t p_bytes = dr.bytes - 256 - (size_t)(t * ldt * 8);
+    for (int64_t c0 = 0; c0 < N; c0 += t) {
+        const int64_t tk = std::min(t, N - c0), rest = N - c0;
+        if (c0 > 0) {
+            // panel -= L[c0:, 0:c0] L[c0:c0+tk, 0:c0]^T on the lower triangle (upper: the transposed form)
+            if (!upper)
+                rc = dr.gemm('N', 'T', rest, tk, c0, -1.0, A + c0 * lda, lda, A + c0 * lda, lda, 1.0,
+                             A + c0 * lda + c0, lda, 1);
+            else
+                rc = dr.gemm('T', 'N', tk, rest, c0, -1.0, A + c0, lda, A + c0, lda, 1.0, A + c0 * lda + c0, lda, 2);
+            if (rc) return rc;
+        }
+        // factor the diagonal block
+        double* hD = A + c0 * lda + c0;
+        if ((rc = dr.copy_in(dT, ldt, hD, lda, tk, tk))) return rc;
+        if ((rc = incore_potrf(upper, dT, ldt, tk, c0, dr.d, why))) return fail(rc, why);
+        if ((rc = dr.copy_out(hD, lda, dT, ldt, tk, tk))) return rc;
+        if ((rc = dr.drain())) return rc;
+        unsigned long long hinfo = 0;
+        if (cudaMemcpy(&hinfo, dr.d.info, sizeof(hinfo), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return fail(OOC_ERR_CUDA, "pivot word read failed");
+        if (hinfo) {
+            *info = (int64_t)hinfo;
+            dr.finish(stats, 0.0);
+            return OOC_OK;
+        }
+        // the rest of the panel: X L11^T = P (lower) or U11^T X = P (upper), in chunks
+        const int64_t nv_total = rest - tk;
+        const int64_t lp = round_up64(tk, 16);
+        const int64_t chunk = upper ? std::max<int64_t>(kSmall, (int64_t)(p_bytes / (8 * (size_t)tk)) / 16 * 16)
+                                    : std::max<int64_t>(kSmall, (int64_t)(p_bytes / (8 * (size_t)lp)));
+        for (int64_t v0 = 0; v0 < nv_total; v0 += chunk) {
+            const int64_t nv = std::min(chunk, nv_total - v0);
+            double* hP = upper ? A + c0 * lda + c0 + tk + v0 : A + (c0 + tk + v0) * lda + c0;
+            const int64_t ldp = upper ? round_up64(nv, 16) : lp;
+            const int64_t rows = upper ? tk : nv, cols = upper ? nv : tk;
+            if ((rc = dr.copy_in(dP, ldp, hP, lda, rows, cols))) return rc;
+            // stored L11 read transposed is upper (right solve); stored U11 read transposed is lower (left solve)
+            if ((rc = incore_trsm(upper, upper, dT, ldt, true, false, tk, dP, ldp, nv, dr.d, why)))
+                return fail(rc, why);
+            if ((rc = dr.copy_out(hP, lda, dP, ldp, rows, cols))) return rc;
+            if ((rc = dr.drain())) return rc;
+        }
+    }
+    dr.finish(stats, (double)N * N * N / 3.0);
+    return OOC_OK;
+}

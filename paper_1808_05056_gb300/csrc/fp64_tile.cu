@@ -8,7 +8,8 @@
 // the tile as 4 x 4 MMA fragments in registers.  The grid is persistent: each
 // CTA walks tiles blockIdx.x, blockIdx.x + gridDim.x, ... with the stage ring
 // running on across tile boundaries, so the copies of the next tile overlap
-// the epilogue of the current one.  Ragged edges come from the tensor maps:
+// the epilogue of the current one (tiles are taken in a grouped raster order,
+// see tile_of).  Ragged edges come from the tensor maps:
 // reads outside the operand are zero-filled by TMA and the epilogue masks
 // stores.
 //
@@ -37,6 +38,52 @@ constexpr int STAGE_B = BN * BK;
 constexpr uint32_t STAGE_BYTES = (STAGE_A + STAGE_B) * 8;
 constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + 2 * STAGES * sizeof(uint64_t) + 1024;
 
+// Tiles of a triangular update (GEMMT / SYRK blocks that straddle the
+// diagonal).  With square tiles of side T, tile (tm, tn) holds an element with
+// col - row <= off (lower) iff tn - tm <= floor((off + T - 1) / T), and one
+// with col - row >= off (upper) iff tn - tm >= ceil((off - T + 1) / T).  So
+// the kept tiles of tile row tm are one run of columns whose length is
+//   lower: clamp(tm + a, 0, tiles_n), starting at column 0,
+//   upper: clamp(a - tm, 0, tiles_n), ending at the last column,
+// and the run lengths have closed-form prefix sums, which map a kept-tile
+// index to its (tm, tn) by a binary search over tile rows.
+struct TriTiles {
+    int mode;  // 0 every tile, 1 lower, 2 upper
+    int64_t a, tiles_m, tiles_n;
+};
+
+__host__ __device__ inline int64_t clamp64(int64_t v, int64_t lo, int64_t hi) { return v < lo ? lo : (v > hi ? hi : v); }
+__host__ __device__ inline int64_t floor_div(int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+__host__ __device__ inline int64_t tri_run(const TriTiles& t, int64_t tm)
+{
+    return t.mode == 1 ? clamp64(tm + t.a, 0, t.tiles_n) : clamp64(t.a - tm, 0, t.tiles_n);
+}
+
+// number of kept tiles in tile rows [0, x)
+__host__ __device__ inline int64_t tri_prefix(const TriTiles& t, int64_t x)
+{
+    const int64_t T = t.tiles_n, a = t.a;
+    if (t.mode == 1) {
+        const int64_t z = clamp64(1 - a, 0, x);    // rows before z keep no tile
+        const int64_t s = clamp64(T - a, z, x);    // rows from s on keep all T
+        const int64_t n = s - z;
+        return n * (z + s - 1) / 2 + n * a + (x - s) * T;
+    }
+    const int64_t s = clamp64(a - T + 1, 0, x);    // rows before s keep all T
+    const int64_t z = clamp64(a, s, x);            // rows from z on keep none
+    const int64_t n = z - s;
+    return s * T + n * a - n * (s + z - 1) / 2;
+}
+
+__host__ __device__ inline TriTiles tri_tiles(int mode, int64_t off, int64_t tiles_m, int64_t tiles_n, int64_t T)
+{
+    TriTiles t{mode, 0, tiles_m, tiles_n};
+    if (mode == 1) t.a = floor_div(off + T - 1, T) + 1;
+    else if (mode == 2) t.a = tiles_n + floor_div(-(off - T + 1), T);  // tiles_n - ceil((off - T + 1) / T)
+    return t;
+}
+
 struct Fp64Args {
     int64_t M, N, K;
     int64_t tiles_n, tiles;
@@ -45,7 +92,43 @@ struct Fp64Args {
     double* C;
     int64_t ldc;
     int* err;
+    int tri;          // 0 full update, 1 lower (col - row <= tri_off), 2 upper (col - row >= tri_off)
+    int64_t tri_off;
+    TriTiles tt;
 };
+
+// Tile order of a full update: groups of kRasterRows tile rows, column-major
+// inside a group, so that the ~456 tiles in flight span 16 rows and ~29
+// columns and re-read their A and B tiles from L2 rather than DRAM.
+constexpr int64_t kRasterRows = 16;
+
+__device__ __forceinline__ void tile_of(const Fp64Args& p, int64_t tile, int64_t& tm, int64_t& tn)
+{
+    if (p.tri == 0) {
+        const int64_t tiles_m = p.tiles / p.tiles_n;
+        const int64_t per_group = kRasterRows * p.tiles_n;
+        const int64_t g = tile / per_group, r = tile % per_group;
+        const int64_t first = g * kRasterRows;
+        const int64_t rows = tiles_m - first < kRasterRows ? tiles_m - first : kRasterRows;
+        tm = first + r % rows;
+        tn = r / rows;
+        return;
+    }
+    int64_t lo = 0, hi = p.tt.tiles_m - 1;  // largest tm with prefix(tm) <= tile
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (tri_prefix(p.tt, mid) <= tile) lo = mid;
+        else hi = mid - 1;
+    }
+    tm = lo;
+    const int64_t first = p.tri == 1 ? 0 : p.tiles_n - tri_run(p.tt, lo);
+    tn = first + (tile - tri_prefix(p.tt, lo));
+}
+
+__device__ __forceinline__ bool kept(const Fp64Args& p, int64_t row, int64_t col)
+{
+    return p.tri == 0 || (p.tri == 1 ? col - row <= p.tri_off : col - row >= p.tri_off);
+}
 
 __device__ __forceinline__ void dmma_8x8x4(double& d0, double& d1, double a, double b)
 {
@@ -94,7 +177,9 @@ __global__ void __launch_bounds__(THREADS) fp64_tile_kernel(const __grid_constan
                 if (!mbar_wait(&empty[s], ph ^ 1u, p.err, kErrWaitEmpty)) { ok = false; break; }
                 const int64_t tl = it / nk, ks = it % nk;
                 const int64_t tile = blockIdx.x + tl * gridDim.x;
-                const int32_t tm = (int32_t)(tile / p.tiles_n), tn = (int32_t)(tile % p.tiles_n);
+                int64_t tm64, tn64;
+                tile_of(p, tile, tm64, tn64);
+                const int32_t tm = (int32_t)tm64, tn = (int32_t)tn64;
                 double* sA = stages + (size_t)s * (STAGE_A + STAGE_B);
                 double* sB = sA + STAGE_A;
                 mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
@@ -128,14 +213,24 @@ __global__ void __launch_bounds__(THREADS) fp64_tile_kernel(const __grid_constan
         for (int b = 0; b < 4; ++b) acc[a][b][0] = acc[a][b][1] = 0.0;
 
     auto epilogue = [&](int64_t tile) {
-        const int64_t tm = tile / p.tiles_n, tn = tile % p.tiles_n;
+        int64_t tm, tn;
+        tile_of(p, tile, tm, tn);
 #pragma unroll
         for (int mi = 0; mi < 4; ++mi) {
             const int64_t row = tm * BM + wm * 32 + mi * 8 + fr;
 #pragma unroll
             for (int ni = 0; ni < 4; ++ni) {
                 const int64_t col = tn * BN + wn * 32 + ni * 8 + fc * 2;
-                if (row < p.M) {
+                if (row < p.M && p.tri != 0) {  // masked: element by element
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        if (col + e >= p.N || !kept(p, row, col + e)) continue;
+                        double* c = p.C + row * p.ldc + col + e;
+                        double v = p.alpha * acc[mi][ni][e];
+                        if (p.read_c) v += p.beta * c[0];
+                        c[0] = v;
+                    }
+                } else if (row < p.M) {
                     double* c = p.C + row * p.ldc + col;
                     if (col + 1 < p.N) {
                         double2 v;
@@ -222,9 +317,11 @@ int launch_variant(const CUtensorMap& ma, const CUtensorMap& mb, const Fp64Args&
 
 int launch_fp64_tile(bool a_kmajor, bool b_kmajor, int64_t M, int64_t N, int64_t K, double alpha,
                      const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
-                     bool read_c, double* C, int64_t ldc, int* err, void* stream, std::string& why)
+                     bool read_c, double* C, int64_t ldc, int* err, void* stream, std::string& why, int tri,
+                     int64_t tri_off)
 {
     if (M <= 0 || N <= 0) return OOC_OK;
+    static_assert(BM == BN, "the triangular tile map assumes square tiles");
     CUtensorMap ma, mbm;
     std::memset(&ma, 0, sizeof(ma));
     std::memset(&mbm, 0, sizeof(mbm));
@@ -242,6 +339,12 @@ int launch_fp64_tile(bool a_kmajor, bool b_kmajor, int64_t M, int64_t N, int64_t
     a.tiles = ((M + BM - 1) / BM) * a.tiles_n;
     a.alpha = alpha; a.beta = beta; a.read_c = read_c ? 1 : 0;
     a.C = C; a.ldc = ldc; a.err = err;
+    a.tri = tri; a.tri_off = tri_off;
+    a.tt = tri_tiles(tri, tri_off, (M + BM - 1) / BM, a.tiles_n, BM);
+    if (tri) {
+        a.tiles = tri_prefix(a.tt, a.tt.tiles_m);
+        if (a.tiles == 0) return OOC_OK;  // nothing of C is updated
+    }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (a_kmajor && b_kmajor) return launch_variant<true, true>(ma, mbm, a, st, why);
     if (a_kmajor && !b_kmajor) return launch_variant<true, false>(ma, mbm, a, st, why);

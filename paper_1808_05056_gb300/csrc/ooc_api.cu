@@ -391,6 +391,10 @@ int launch_split_tile(const Plan& p, const Op& op, Exec& x, const Operands& o, i
     P.err = err;
     P.kblock = 64;
     P.pair = (x.flags & OOC_TC_PAIR) != 0;
+    if (p.block_class(op.i, op.j) == 2) {
+        P.tri = p.tri;
+        P.tri_off = p.block_off(op.i, op.j);
+    }
     ++x.launches;
     return launch_tc_terms(P, st, why);
 }
@@ -412,8 +416,10 @@ int launch_tile(const Plan& p, const Op& op, Exec& x, const Operands& o, std::st
         const double* dB = sb >= 0 ? reinterpret_cast<const double*>(x.base + slot_offset(p, sb)) : nullptr;
         double* dC = reinterpret_cast<double*>(x.base + slot_offset(p, sc));
         ++x.launches;
+        const bool masked = p.block_class(op.i, op.j) == 2;
         return launch_fp64_tile(!p.ta, p.tb, rows, cols, kk, o.alpha, dA, p.lda_dev, dB, p.ldb_dev, beta_eff, read_c,
-                                dC, p.ldc_dev, err, x.smap[kStreamCompute], why);
+                                dC, p.ldc_dev, err, x.smap[kStreamCompute], why, masked ? p.tri : 0,
+                                masked ? p.block_off(op.i, op.j) : 0);
     }
     why = "contraction form not available in this build";
     return OOC_ERR_UNSUPPORTED;
@@ -507,8 +513,9 @@ int issue_ops(Exec& x, const Plan& p, const std::vector<Op>& ops, const Operands
     return OOC_OK;
 }
 
+// tri / tri_off: triangular update of C (Plan::tri); 0 updates all of C.
 int run_ooc(char ta, char tb, int64_t M, int64_t N, int64_t K, const Operands& o, int es, size_t budget,
-            const ooc_opts* opts_in, ooc_stats* stats)
+            const ooc_opts* opts_in, ooc_stats* stats, int tri = 0, int64_t tri_off = 0)
 {
     const auto t_host0 = std::chrono::steady_clock::now();
     std::string why;
@@ -527,6 +534,7 @@ int run_ooc(char ta, char tb, int64_t M, int64_t N, int64_t K, const Operands& o
     if (opts_in) opts = *opts_in;
     PlanRequest rq{M, N, K, es, o.beta != 0.0, is_t(ta), is_t(tb), budget, opts};
     rq.lda = o.lda; rq.ldb = o.ldb; rq.ldc = o.ldc;
+    rq.tri = tri; rq.tri_off = tri_off;
     double hg = 0, dg = 0;
     if (ooc_query_device(nullptr, &hg, &dg) == OOC_OK && hg > 0 && dg > 0) {
         rq.h2d_gbps = hg;
@@ -619,7 +627,9 @@ int run_ooc(char ta, char tb, int64_t M, int64_t N, int64_t K, const Operands& o
         stats->d2h_bytes = x.d2h;
         stats->mb = p.mb; stats->nb = p.nb; stats->kb = p.kb;
         stats->depth = p.nA; stats->c_buffers = p.nC; stats->b_buffers = p.nB; stats->form = p.form;
-        stats->blocks = p.h * p.w; stats->steps = p.h * p.w * p.nkc;
+        int64_t nblk = 0;
+        for (const Op& op : ops) nblk += op.kind == kD2H;
+        stats->blocks = nblk; stats->steps = x.n_kern;
         stats->device_bytes = (int64_t)p.device_bytes;
         stats->slices = p.slices; stats->products = p.products;
         stats->kernel_launches = x.launches;
@@ -628,10 +638,32 @@ int run_ooc(char ta, char tb, int64_t M, int64_t N, int64_t K, const Operands& o
     x.release();
     if (stats) {
         stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_host0).count();
-        stats->tflops = stats->seconds > 0 ? 2.0 * (double)M * N * K / stats->seconds / 1e12 : 0.0;
+        // a triangular update of a square C counts N (N + 1) K flops (the level-3 BLAS convention for SYRK)
+        const double flops = tri ? (double)M * (M + 1) * K : 2.0 * (double)M * N * K;
+        stats->tflops = stats->seconds > 0 ? flops / stats->seconds / 1e12 : 0.0;
     }
     return OOC_OK;
 }
+
+}  // namespace
+
+namespace ooc {
+bool host_range_pinned(const void* base, int64_t rows, int64_t cols, int64_t ld, int es)
+{
+    return range_pinned(base, rows, cols, ld, es);
+}
+int device_check(std::string& why) { return check_device(why); }
+
+int run_gemm_host(char ta, char tb, int64_t M, int64_t N, int64_t K, double alpha, const void* A, int64_t lda,
+                  const void* B, int64_t ldb, double beta, void* C, int64_t ldc, int es, size_t budget,
+                  const ooc_opts* opts, ooc_stats* stats, int tri, int64_t tri_off)
+{
+    Operands o{A, lda, B, ldb, C, ldc, alpha, beta};
+    return run_ooc(ta, tb, M, N, K, o, es, budget, opts, stats, tri, tri_off);
+}
+}  // namespace ooc
+
+namespace {
 
 int run_batched(int32_t count, const ooc_gemm_desc* d, size_t budget, const ooc_opts* opts_in, ooc_stats* stats)
 {
@@ -937,43 +969,30 @@ const char* ooc_strerror(int code)
 
 const char* ooc_last_error(void) { return g_last_error.c_str(); }
 
-int ooc_plan(int64_t M, int64_t N, int64_t K, int32_t elem_bytes, int32_t beta_nonzero, size_t budget,
-             const ooc_opts* opts_in, ooc_stats* out)
+namespace {
+
+void fill_plan_stats(const Plan& p, ooc_stats* out)
 {
-    if ((elem_bytes != 4 && elem_bytes != 8) || M <= 0 || N <= 0 || K < 0 || !out)
-        return fail(OOC_ERR_INVALID_ARG, "ooc_plan: bad arguments");
-    ooc_opts opts;
-    std::memset(&opts, 0, sizeof(opts));
-    if (opts_in) opts = *opts_in;
-    PlanRequest rq{M, N, K, elem_bytes, beta_nonzero != 0, false, false, budget, opts};
-    Plan p;
-    std::string why;
-    int rc = make_plan(rq, p, why);
-    if (rc) return fail(rc, why);
     std::memset(out, 0, sizeof(*out));
     out->mb = p.mb; out->nb = p.nb; out->kb = p.kb;
     out->depth = p.nA; out->c_buffers = p.nC; out->b_buffers = p.nB; out->form = p.form;
-    out->blocks = p.h * p.w; out->steps = p.h * p.w * p.nkc;
+    int64_t nblk = 0;
+    for (int64_t j = 0; j < p.w; ++j)
+        for (int64_t i = 0; i < p.h; ++i) nblk += p.block_class(i, j) != 0;
+    out->blocks = nblk; out->steps = nblk * p.nkc;
     out->device_bytes = (int64_t)p.device_bytes;
     out->h2d_bytes = p.h2d_bytes; out->d2h_bytes = p.d2h_bytes;
     out->slices = p.slices; out->products = p.products;
     out->seconds = p.est_seconds;
-    return OOC_OK;
 }
 
-int ooc_schedule(int64_t M, int64_t N, int64_t K, int32_t elem_bytes, int32_t beta_nonzero, size_t budget,
-                 const ooc_opts* opts_in, ooc_sched_op* out, int64_t capacity, int64_t* count)
+int export_schedule(const PlanRequest& rq, ooc_stats* plan_out, ooc_sched_op* out, int64_t capacity, int64_t* count)
 {
-    if ((elem_bytes != 4 && elem_bytes != 8) || M <= 0 || N <= 0 || K < 0 || !count)
-        return fail(OOC_ERR_INVALID_ARG, "ooc_schedule: bad arguments");
-    ooc_opts opts;
-    std::memset(&opts, 0, sizeof(opts));
-    if (opts_in) opts = *opts_in;
-    PlanRequest rq{M, N, K, elem_bytes, beta_nonzero != 0, false, false, budget, opts};
     Plan p;
     std::string why;
     int rc = make_plan(rq, p, why);
     if (rc) return fail(rc, why);
+    if (plan_out) fill_plan_stats(p, plan_out);
     std::vector<Op> ops;
     build_schedule(p, ops);
     *count = (int64_t)ops.size();
@@ -992,6 +1011,52 @@ int ooc_schedule(int64_t M, int64_t N, int64_t K, int32_t elem_bytes, int32_t be
         }
     }
     return OOC_OK;
+}
+
+int uplo_code(char uplo) { return (uplo == 'L' || uplo == 'l') ? 1 : (uplo == 'U' || uplo == 'u') ? 2 : 0; }
+
+}  // namespace
+
+int ooc_plan(int64_t M, int64_t N, int64_t K, int32_t elem_bytes, int32_t beta_nonzero, size_t budget,
+             const ooc_opts* opts_in, ooc_stats* out)
+{
+    if ((elem_bytes != 4 && elem_bytes != 8) || M <= 0 || N <= 0 || K < 0 || !out)
+        return fail(OOC_ERR_INVALID_ARG, "ooc_plan: bad arguments");
+    ooc_opts opts;
+    std::memset(&opts, 0, sizeof(opts));
+    if (opts_in) opts = *opts_in;
+    PlanRequest rq{M, N, K, elem_bytes, beta_nonzero != 0, false, false, budget, opts};
+    Plan p;
+    std::string why;
+    int rc = make_plan(rq, p, why);
+    if (rc) return fail(rc, why);
+    fill_plan_stats(p, out);
+    return OOC_OK;
+}
+
+int ooc_schedule(int64_t M, int64_t N, int64_t K, int32_t elem_bytes, int32_t beta_nonzero, size_t budget,
+                 const ooc_opts* opts_in, ooc_sched_op* out, int64_t capacity, int64_t* count)
+{
+    if ((elem_bytes != 4 && elem_bytes != 8) || M <= 0 || N <= 0 || K < 0 || !count)
+        return fail(OOC_ERR_INVALID_ARG, "ooc_schedule: bad arguments");
+    ooc_opts opts;
+    std::memset(&opts, 0, sizeof(opts));
+    if (opts_in) opts = *opts_in;
+    PlanRequest rq{M, N, K, elem_bytes, beta_nonzero != 0, false, false, budget, opts};
+    return export_schedule(rq, nullptr, out, capacity, count);
+}
+
+int ooc_schedule_gemmt(char uplo, int64_t N, int64_t K, int32_t elem_bytes, int32_t beta_nonzero, size_t budget,
+                       const ooc_opts* opts_in, ooc_stats* plan, ooc_sched_op* out, int64_t capacity, int64_t* count)
+{
+    if ((elem_bytes != 4 && elem_bytes != 8) || N <= 0 || K < 0 || !count || !uplo_code(uplo))
+        return fail(OOC_ERR_INVALID_ARG, "ooc_schedule_gemmt: bad arguments");
+    ooc_opts opts;
+    std::memset(&opts, 0, sizeof(opts));
+    if (opts_in) opts = *opts_in;
+    PlanRequest rq{N, N, K, elem_bytes, beta_nonzero != 0, false, false, budget, opts};
+    rq.tri = uplo_code(uplo);
+    return export_schedule(rq, plan, out, capacity, count);
 }
 
 int ooc_query_device(size_t* free_bytes, double* h2d_gbps, double* d2h_gbps)
@@ -1061,6 +1126,37 @@ int ooc_sgemm(char transA, char transB, int64_t M, int64_t N, int64_t K, float a
 {
     Operands o{A, lda, B, ldb, C, ldc, (double)alpha, (double)beta};
     return run_ooc(transA, transB, M, N, K, o, 4, device_budget_bytes, opts, stats);
+}
+
+int ooc_dgemmt(char uplo, char transA, char transB, int64_t N, int64_t K, double alpha, const double* A, int64_t lda,
+               const double* B, int64_t ldb, double beta, double* C, int64_t ldc, size_t device_budget_bytes,
+               const ooc_opts* opts, ooc_stats* stats)
+{
+    const int tri = uplo_code(uplo);
+    if (!tri) return fail(OOC_ERR_INVALID_ARG, "uplo must be 'L' or 'U'");
+    Operands o{A, lda, B, ldb, C, ldc, alpha, beta};
+    return run_ooc(transA, transB, N, N, K, o, 8, device_budget_bytes, opts, stats, tri, 0);
+}
+
+int ooc_dsyrk(char uplo, char trans, int64_t N, int64_t K, double alpha, const double* A, int64_t lda, double beta,
+              double* C, int64_t ldc, size_t device_budget_bytes, const ooc_opts* opts, ooc_stats* stats)
+{
+    const int tri = uplo_code(uplo);
+    if (!tri) return fail(OOC_ERR_INVALID_ARG, "uplo must be 'L' or 'U'");
+    if (!is_n(trans) && !is_t(trans)) return fail(OOC_ERR_INVALID_ARG, "trans must be 'N' or 'T'");
+    // op(A) op(A)^T: the second operand is the same host matrix with the other transpose
+    Operands o{A, lda, A, lda, C, ldc, alpha, beta};
+    return run_ooc(trans, is_n(trans) ? 'T' : 'N', N, N, K, o, 8, device_budget_bytes, opts, stats, tri, 0);
+}
+
+int ooc_ssyrk(char uplo, char trans, int64_t N, int64_t K, float alpha, const float* A, int64_t lda, float beta,
+              float* C, int64_t ldc, size_t device_budget_bytes, const ooc_opts* opts, ooc_stats* stats)
+{
+    const int tri = uplo_code(uplo);
+    if (!tri) return fail(OOC_ERR_INVALID_ARG, "uplo must be 'L' or 'U'");
+    if (!is_n(trans) && !is_t(trans)) return fail(OOC_ERR_INVALID_ARG, "trans must be 'N' or 'T'");
+    Operands o{A, lda, A, lda, C, ldc, (double)alpha, (double)beta};
+    return run_ooc(trans, is_n(trans) ? 'T' : 'N', N, N, K, o, 4, device_budget_bytes, opts, stats, tri, 0);
 }
 
 int ooc_dgemm_device(char transA, char transB, int64_t M, int64_t N, int64_t K, double alpha, const double* dA,

@@ -36,11 +36,28 @@ struct Plan {
     double est_seconds = 0;
     // device leading dimensions (elements) of the slots, per stored layout
     int64_t lda_dev = 0, ldb_dev = 0, ldc_dev = 0;
+    // Triangular update (GEMMT / SYRK): only elements with col - row <= tri_off
+    // (tri 1, lower) or col - row >= tri_off (tri 2, upper) of C are updated.
+    int32_t tri = 0;
+    int64_t tri_off = 0;
 
     int64_t rows_of(int64_t i) const { return (i + 1) * mb <= M ? mb : M - i * mb; }
     int64_t cols_of(int64_t j) const { return (j + 1) * nb <= N ? nb : N - j * nb; }
     int64_t k_of(int64_t c) const { return (c + 1) * kb <= K ? kb : K - c * kb; }
     int32_t slots() const { return nA + nB + nC; }
+    // 0: block (i, j) holds no updated element (skipped); 1: all of it is
+    // updated; 2: it straddles the edge of the updated part (masked epilogue,
+    // and the block is loaded so that its other elements go back unchanged)
+    int block_class(int64_t i, int64_t j) const
+    {
+        if (!tri) return 1;
+        const int64_t r0 = i * mb, c0 = j * nb;
+        const int64_t lo = c0 - (r0 + rows_of(i) - 1), hi = c0 + cols_of(j) - 1 - r0;  // min / max of col - row
+        if (tri == 1) return lo > tri_off ? 0 : (hi <= tri_off ? 1 : 2);
+        return hi < tri_off ? 0 : (lo >= tri_off ? 1 : 2);
+    }
+    // the diagonal offset in block (i, j)'s own coordinates
+    int64_t block_off(int64_t i, int64_t j) const { return tri_off + i * mb - j * nb; }
 };
 
 struct PlanRequest {
@@ -51,6 +68,8 @@ struct PlanRequest {
     ooc_opts opts;
     double h2d_gbps = 200.0, d2h_gbps = 190.0;  // link model for the estimate
     int64_t lda = 0, ldb = 0, ldc = 0;          // host leading dimensions (0: rows are contiguous)
+    int32_t tri = 0;                            // triangular update of C (Plan::tri)
+    int64_t tri_off = 0;
 };
 
 // Returns OOC_OK and fills `plan`, or an error code with a message in `why`.
@@ -125,10 +144,12 @@ int encode_map_2d(void* map_out, int dtype /*0 f64, 1 bf16, 2 f32*/, const void*
 // FP64 tile GEMM on device operands (one C block, one K chunk):
 // C = alpha*op(A)*op(B) + (read_c ? beta*C : 0).
 // a_kmajor: A stored rows x K (else K x rows); b_kmajor: B stored cols x K (else K x cols).
+// tri (1 lower, 2 upper) limits the update to elements with col - row <= / >=
+// tri_off; tiles holding no such element are not computed.
 int launch_fp64_tile(bool a_kmajor, bool b_kmajor, int64_t M, int64_t N, int64_t K, double alpha,
                      const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
                      bool read_c, double* C, int64_t ldc, int* err, void* stream,
-                     std::string& why);
+                     std::string& why, int tri = 0, int64_t tri_off = 0);
 
 // --- tensor-core split-product forms (tc_gemm.cu) -------------------------
 // A group: pairs (A plane, B plane) accumulated into one FP32 TMEM accumulator
@@ -162,6 +183,8 @@ struct TcProblem {
     bool df32 = false;                 // two accumulators per group, double-float drain (BF16x3)
     int kblock = 64;                   // K block per pipeline stage: 64 or 32
     bool pair = false;                 // CTA-pair (cta_group::2, 256-row) tiles when the device allows
+    int tri = 0;                       // epilogue mask as in launch_fp64_tile
+    int64_t tri_off = 0;
 };
 
 int tc_max_groups();
@@ -181,5 +204,14 @@ constexpr int kBf16x3Chunk = 128;
 
 int device_sm_count();
 void set_error(const std::string& msg);
+
+bool host_range_pinned(const void* base, int64_t rows, int64_t cols, int64_t ld, int es);
+int device_check(std::string& why);  // OOC_OK when an sm_103 device is current
+
+// The whole out-of-core pipeline on host operands (ooc_dgemm / ooc_sgemm /
+// ooc_dgemmt), for the drivers built on it (TRSM, Cholesky).
+int run_gemm_host(char ta, char tb, int64_t M, int64_t N, int64_t K, double alpha, const void* A, int64_t lda,
+                  const void* B, int64_t ldb, double beta, void* C, int64_t ldc, int es, size_t budget,
+                  const ooc_opts* opts, ooc_stats* stats, int tri, int64_t tri_off);
 
 }  // namespace ooc

@@ -109,17 +109,87 @@ void layout(Plan& p, const FormModel& f)
                      (size_t)p.nB * (p.b_slot + p.b_aux) + (size_t)p.nC * (p.c_slot + p.c_aux);
 }
 
+// The updated blocks of block column j: block rows [lo, hi) are updated, of
+// which those outside [in_lo, in_hi) straddle the edge of a triangular
+// update.  For the lower part both ranges end at the last block row, for the
+// upper part both start at row 0 (min and max of col - row over a block fall
+// as i grows).
+struct ColumnBlocks {
+    int64_t lo, hi, in_lo, in_hi;
+};
+
+ColumnBlocks column_blocks(const Plan& p, int64_t j)
+{
+    if (!p.tri) return {0, p.h, 0, p.h};
+    // first block row at which pred(i) holds (pred turns true once and stays true)
+    auto first = [&](auto pred) {
+        int64_t a = 0, b = p.h;
+        while (a < b) {
+            const int64_t m = (a + b) / 2;
+            if (pred(m)) b = m;
+            else a = m + 1;
+        }
+        return a;
+    };
+    if (p.tri == 1) {
+        const int64_t lo = first([&](int64_t i) { return p.block_class(i, j) != 0; });
+        const int64_t in = first([&](int64_t i) { return p.block_class(i, j) == 1; });
+        return {lo, p.h, std::max(in, lo), p.h};
+    }
+    const int64_t hi = first([&](int64_t i) { return p.block_class(i, j) == 0; });
+    const int64_t in = first([&](int64_t i) { return p.block_class(i, j) != 1; });
+    return {0, hi, 0, std::min(in, hi)};
+}
+
+// rows of block rows [a, b)
+int64_t rows_in(const Plan& p, int64_t a, int64_t b)
+{
+    if (b <= a) return 0;
+    return b == p.h ? p.M - a * p.mb : (b - a) * p.mb;
+}
+
+int64_t active_blocks(const Plan& p)
+{
+    if (!p.tri) return p.h * p.w;
+    int64_t n = 0;
+    for (int64_t j = 0; j < p.w; ++j) {
+        const ColumnBlocks cb = column_blocks(p, j);
+        n += std::max<int64_t>(0, cb.hi - cb.lo);
+    }
+    return n;
+}
+
 // Closed-form traffic of the schedule for this plan.
 void traffic(Plan& p)
 {
     const double es = p.es;
     const double A = (double)p.M * p.K * es, B = (double)p.K * p.N * es, C = (double)p.M * p.N * es;
-    // A chunks are re-sent for every block column unless one column's worth stays resident
-    double a_loads = (p.h == 1 && p.nkc <= p.nA) ? A : A * p.w;
-    double b_loads = (p.nkc <= p.nB) ? B : B * p.h;
+    if (!p.tri) {
+        // A chunks are re-sent for every block column unless one column's worth stays resident
+        double a_loads = (p.h == 1 && p.nkc <= p.nA) ? A : A * p.w;
+        double b_loads = (p.nkc <= p.nB) ? B : B * p.h;
+        if (p.K == 0) a_loads = b_loads = 0;
+        p.h2d_bytes = a_loads + b_loads + (p.beta_nz ? C : 0.0);
+        p.d2h_bytes = C;
+        return;
+    }
+    double a_loads = 0, b_loads = 0, c_in = 0, c_out = 0;
+    for (int64_t j = 0; j < p.w; ++j) {
+        const ColumnBlocks cb = column_blocks(p, j);
+        if (cb.hi <= cb.lo) continue;
+        const double cols = (double)p.cols_of(j);
+        const double rows = (double)rows_in(p, cb.lo, cb.hi);
+        const double straddle = rows - (double)rows_in(p, cb.in_lo, cb.in_hi);
+        a_loads += rows * p.K * es;
+        b_loads += (p.nkc <= p.nB ? 1.0 : (double)(cb.hi - cb.lo)) * p.K * cols * es;
+        c_out += rows * cols * es;
+        c_in += (p.beta_nz ? rows : straddle) * cols * es;
+    }
+    if (p.h == 1 && p.nkc <= p.nA) a_loads = std::min(a_loads, A);
     if (p.K == 0) a_loads = b_loads = 0;
-    p.h2d_bytes = a_loads + b_loads + (p.beta_nz ? C : 0.0);
-    p.d2h_bytes = C;
+    (void)B; (void)C;
+    p.h2d_bytes = a_loads + b_loads + c_in;
+    p.d2h_bytes = c_out;
 }
 
 // Host rows of one copy of `mat` are short and not contiguous.
@@ -147,6 +217,18 @@ double estimate(const Plan& p, const FormModel& f, int sms, double h2d_gbps, dou
     struct Part { int64_t rows, cols, count; };
     Part parts[4] = {{p.mb, p.nb, hf * wf}, {mr, p.nb, (mr ? 1 : 0) * wf},
                      {p.mb, nr, hf * (nr ? 1 : 0)}, {mr, nr, (mr && nr) ? 1 : 0}};
+    if (p.tri) {  // count only the updated blocks (straddling ones as whole blocks)
+        for (auto& pt : parts) pt.count = 0;
+        for (int64_t j = 0; j < p.w; ++j) {
+            const ColumnBlocks cb = column_blocks(p, j);
+            if (cb.hi <= cb.lo) continue;
+            const bool rag_col = p.cols_of(j) != p.nb;
+            const bool rag_row = cb.hi == p.h && mr != 0;
+            const int64_t full_rows = cb.hi - cb.lo - (rag_row ? 1 : 0);
+            parts[rag_col ? 2 : 0].count += full_rows;
+            if (rag_row) parts[rag_col ? 3 : 1].count += 1;
+        }
+    }
     const double tile_time_per_k = 2.0 * f.tile_m * f.tile_n * slots_total / f.rate;
     for (auto& pt : parts) {
         if (pt.count == 0 || pt.rows == 0 || pt.cols == 0) continue;
@@ -162,18 +244,25 @@ double estimate(const Plan& p, const FormModel& f, int sms, double h2d_gbps, dou
     const double drain = (double)p.mb * p.nb * es / bw_d;
     double bubbles = 0;
     if (p.nB < 2 * p.nkc && p.nkc <= p.nB) bubbles = (double)(p.w - 1) * p.K * p.nb * es / bw_h;
-    const double steps = (double)p.h * p.w * p.nkc;
+    const double steps = (double)active_blocks(p) * p.nkc;
     // Strided host copies with short rows (< 64 KiB) run far below the link
     // rate on this host link and were seen to slow down further as more host
     // memory is touched; charge them at a quarter of the link rate, outside
     // the overlap.
     double narrow = 0;
     const double A = (double)p.M * p.K * es, B = (double)p.K * p.N * es, C = (double)p.M * p.N * es;
-    const double a_loads = (p.h == 1 && p.nkc <= p.nA) ? A : A * p.w;
-    const double b_loads = (p.nkc <= p.nB) ? B : B * p.h;
+    double a_loads = (p.h == 1 && p.nkc <= p.nA) ? A : A * p.w;
+    double b_loads = (p.nkc <= p.nB) ? B : B * p.h;
+    double c_moved = C * (p.beta_nz ? 2.0 : 1.0);
+    if (p.tri) {  // the traffic model already counts the updated blocks only
+        const double c_frac = p.d2h_bytes / std::max(C, 1.0);
+        a_loads *= c_frac;
+        b_loads *= c_frac;
+        c_moved = p.d2h_bytes * (p.beta_nz ? 2.0 : 1.0);
+    }
     if (narrow_rows(p, kMatA)) narrow += a_loads;
     if (narrow_rows(p, kMatB)) narrow += b_loads;
-    if (narrow_rows(p, kMatC)) narrow += C * (p.beta_nz ? 2.0 : 1.0);
+    if (narrow_rows(p, kMatC)) narrow += c_moved;
     return std::max(t_comp, t_link) + fill + drain + bubbles + steps * 8e-6 + narrow / (0.25 * bw_h);
 }
 
@@ -214,6 +303,7 @@ int make_plan(const PlanRequest& rq, Plan& p, std::string& why)
     p = Plan{};
     p.M = rq.M; p.N = rq.N; p.K = rq.K; p.es = rq.es;
     p.beta_nz = rq.beta_nz; p.ta = rq.ta; p.tb = rq.tb;
+    p.tri = rq.tri; p.tri_off = rq.tri_off;
     p.lda_host = rq.lda; p.ldb_host = rq.ldb; p.ldc_host = rq.ldc;
     int form = rq.opts.form;
     if (form == OOC_FORM_AUTO) form = (rq.es == 8) ? OOC_FORM_FP64 : OOC_FORM_BF16X3;
@@ -314,7 +404,7 @@ int make_plan(const PlanRequest& rq, Plan& p, std::string& why)
         return OOC_ERR_BUDGET;
     }
     p = best;
-    if (!keep && (rq.opts.flags & OOC_PLAN_MODEL)) {
+    if (!keep && (rq.opts.flags & OOC_PLAN_MODEL) && !rq.tri) {  // the model is trained on full updates
         std::vector<float> params;
         if (costmodel_get(params)) {
             std::vector<Plan> cands;
@@ -481,10 +571,14 @@ struct Gen {
     {
         const int a0 = 0, b0 = p.nA, c0 = p.nA + p.nB;
         const bool have_k = p.K > 0;
+        int64_t nblk = 0;  // blocks issued so far: C blocks take the C slots in turn
         for (int64_t j = 0; j < p.w; ++j)
             for (int64_t i = 0; i < p.h; ++i) {
-                const int64_t blk = j * p.h + i;
-                const int sc = c0 + (int)(blk % p.nC);
+                const int cls = p.block_class(i, j);
+                if (cls == 0) continue;  // no element of this block is updated
+                // a block straddling a triangular update's edge goes back whole, so it is loaded even for beta == 0
+                const bool load_c = p.beta_nz || cls == 2;
+                const int sc = c0 + (int)(nblk++ % p.nC);
                 for (int64_t kc = 0; kc < p.nkc; ++kc) {
                     const int64_t t = step_index(i, j, kc);
                     int sa = -1, sb = -1;
@@ -494,7 +588,7 @@ struct Gen {
                     }
                     if (kc == 0) {
                         const Tag ct{kMatC, i, j, 0};
-                        if (p.beta_nz) {
+                        if (load_c) {
                             if (d2h_pending[sc]) emit_wait(kStreamH2D, ev_out(p, sc));
                             Op o; o.kind = kH2D; o.stream = kStreamH2D; o.wslot = sc; o.wtag = ct;
                             o.i = i; o.j = j; o.kc = 0;
@@ -523,7 +617,7 @@ struct Gen {
                     k.first = (kc == 0); k.last = (kc == p.nkc - 1);
                     if (sa >= 0) { k.rslot[k.nr] = sa; k.rtag[k.nr] = content[sa]; ++k.nr; }
                     if (sb >= 0) { k.rslot[k.nr] = sb; k.rtag[k.nr] = content[sb]; ++k.nr; }
-                    if (kc > 0 || p.beta_nz) { k.rslot[k.nr] = sc; k.rtag[k.nr] = content[sc]; ++k.nr; }
+                    if (kc > 0 || load_c) { k.rslot[k.nr] = sc; k.rtag[k.nr] = content[sc]; ++k.nr; }
                     k.wslot = sc;
                     k.wtag = Tag{kMatC, i, j, kc + 1};
                     push(k);

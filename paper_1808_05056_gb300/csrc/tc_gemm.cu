@@ -85,6 +85,8 @@ struct TcArgs {
     const int* row_exp;
     const int* col_exp;
     int* err;
+    int tri;          // 0 full update, 1 lower (col - row <= tri_off), 2 upper (col - row >= tri_off)
+    int64_t tri_off;
     TcGroup g[MAX_GROUPS];
 };
 
@@ -381,7 +383,8 @@ __global__ void __launch_bounds__(THREADS, 1) tc_terms_kernel(const __grid_const
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
                     const int64_t col = col0 + j;
-                    if (col < p.N) {
+                    const bool keep = p.tri == 0 || (p.tri == 1 ? col - row <= p.tri_off : col - row >= p.tri_off);
+                    if (col < p.N && keep) {
                         double a;
                         if constexpr (DF32) a = (double)hi[j] + (double)lo[j];
                         else a = acc[j];
@@ -655,6 +658,7 @@ int launch_tc_terms(const TcProblem& P, void* stream, std::string& why)
     a.C = P.C; a.ldc = P.ldc;
     a.row_exp = P.row_exp; a.col_exp = P.col_exp;
     a.err = P.err;
+    a.tri = P.tri; a.tri_off = P.tri_off;
 
     CUtensorMap ma, mb;
     std::memset(&ma, 0, sizeof(ma));

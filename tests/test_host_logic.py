@@ -197,3 +197,67 @@ def test_operand_loads_never_wait_for_the_kernel_just_issued(M, N, K, es, beta, 
                 waited_kernel = recorded_after[pending_wait] - 1
                 assert waited_kernel <= kernels_issued - 2, (o["write_tag"], waited_kernel, kernels_issued)
             pending_wait = None
+
+
+# ---- triangular updates (GEMMT / SYRK) -----------------------------------
+def _classify(N, mb, nb, i, j, uplo):
+    """0: no element of block (i, j) is updated, 1: all are, 2: some are."""
+    rows = range(i * mb, min(N, (i + 1) * mb))
+    cols = range(j * nb, min(N, (j + 1) * nb))
+    # the updated set of a rectangle is decided by its extreme values of col - row
+    lo, hi = cols[0] - rows[-1], cols[-1] - rows[0]
+    if uplo == "L":
+        return 0 if lo > 0 else (1 if hi <= 0 else 2)
+    return 0 if hi < 0 else (1 if lo >= 0 else 2)
+
+
+TRI_CASES = [
+    # (uplo, N, K, beta, opts)
+    ("L", 300, 170, 0, dict(mb=64, nb=64, kb=64, depth=2, c_buffers=2)),
+    ("U", 300, 170, 1, dict(mb=64, nb=64, kb=64, depth=2, c_buffers=2)),
+    ("L", 333, 90, 0, dict(mb=96, nb=160, kb=90, depth=3, c_buffers=3)),
+    ("U", 333, 90, 0, dict(mb=160, nb=96, kb=32, depth=2, c_buffers=2)),
+    ("L", 1000, 500, 1, {}),
+    ("U", 4096, 1024, 0, {}),
+]
+
+
+@pytest.mark.parametrize("case", range(len(TRI_CASES)))
+def test_triangular_schedule_updates_exactly_the_triangle(case):
+    uplo, N, K, beta, kw = TRI_CASES[case]
+    budget = (1 << 40) if kw else (8 << 20)
+    plan, ops = P.ooc_schedule_gemmt(uplo, N, K, 8, beta, budget, P.make_opts(**kw))
+    mb, nb = plan["mb"], plan["nb"]
+    h, w = -(-N // mb), -(-N // nb)
+    cls = {(i, j): _classify(N, mb, nb, i, j, uplo) for i in range(h) for j in range(w)}
+    active = {b for b, c in cls.items() if c}
+    chk = to_checker(ops)
+    assert pipeline.check(chk) == []
+    nkc = plan["steps"] // plan["blocks"]
+    finals = sorted(t for _, t in pipeline.final_host_writes(chk))
+    assert finals == sorted((2, i, j, nkc) for i, j in active)
+    assert plan["blocks"] == len(active)
+    loaded_c = {(o["write_tag"][1], o["write_tag"][2]) for o in ops if o["kind"] == 0 and o["write_tag"][0] == 2}
+    straddling = {b for b, c in cls.items() if c == 2}
+    assert loaded_c == (active if beta else straddling)
+    # blocks with no updated element are never touched
+    touched = {(o["write_tag"][1], o["write_tag"][2]) for o in ops if o["write_tag"][0] == 2}
+    assert touched <= active
+    if any(c == 0 for c in cls.values()):
+        assert len(active) < h * w
+
+
+def test_triangular_schedule_waits_are_all_needed():
+    _, ops = P.ooc_schedule_gemmt("L", 333, 90, 8, 0, 1 << 40,
+                                  P.make_opts(mb=96, nb=160, kb=32, depth=2, c_buffers=2))
+    chk = to_checker(ops)
+    waits = [k for k, o in enumerate(chk) if o["kind"] == "wait"]
+    assert waits and all(pipeline.check(chk[:k] + chk[k + 1:]) for k in waits)
+
+
+def test_triangular_plan_moves_about_half_the_bytes():
+    full = P.ooc_plan(16384, 16384, 4096, 8, 0, 1 << 30, P.make_opts(mb=2048, nb=2048, kb=4096))
+    tri, _ = P.ooc_schedule_gemmt("L", 16384, 4096, 8, 0, 1 << 30, P.make_opts(mb=2048, nb=2048, kb=4096))
+    assert tri["blocks"] == 8 * 9 // 2 and full["blocks"] == 64
+    assert tri["d2h_bytes"] == pytest.approx(full["d2h_bytes"] * 36 / 64)
+    assert tri["seconds"] < 0.7 * full["seconds"]
