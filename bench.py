@@ -43,10 +43,17 @@ CONFIGS = {
     "bf16x3-65536": ("bf16x3", 65536, 65536, 65536, 1.0, 1.0, 8 << 30, synth.UNIFORM),
     # 256 uneven FP64 problems, M, N, K log-uniform in [512, 32768], ~64 GiB host in total
     "batched-256": ("batched", 256, 512, 32768, 1.0, 0.0, 8 << 30, synth.NORMAL),
+    # level-3 operations on the same pipeline (M = order, N = right-hand sides / K = inner dimension)
+    "syrk-32768": ("syrk", 32768, 32768, 16384, 1.0, 0.5, 4 << 30, synth.NORMAL),
+    "trsm-32768": ("trsm", 32768, 32768, 0, 1.0, 0.0, 4 << 30, synth.UNIFORM),
+    "potrf-32768": ("potrf", 32768, 32768, 0, 1.0, 0.0, 4 << 30, synth.NORMAL),
 }
+LEVEL3 = ("syrk", "trsm", "potrf")
 # per form: (element dtype name, relative Frobenius tolerance, products per logical product, dtype tag)
 FORMS = {"fp64": ("float64", 1e-13, 1, "f64"), "ozaki": ("float64", 1e-12, 36, "f64 (bf16 digit planes)"),
-         "bf16x3": ("float32", 1e-6, 6, "f32 (bf16x3 pieces)"), "batched": ("float64", 1e-13, 1, "f64")}
+         "bf16x3": ("float32", 1e-6, 6, "f32 (bf16x3 pieces)"), "batched": ("float64", 1e-13, 1, "f64"),
+         "syrk": ("float64", 1e-13, 1, "f64"), "trsm": ("float64", 1e-12, 1, "f64"),
+         "potrf": ("float64", 1e-12, 1, "f64")}
 
 
 def batch_shapes(seed, count, lo, hi, cap=64 << 30, es=8):
@@ -63,6 +70,11 @@ def batch_shapes(seed, count, lo, hi, cap=64 << 30, es=8):
             used += fp
     return out
 NOMINAL_FP64_TF, NOMINAL_BF16_TF = 1.25, 2250.0
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the
+# dominant kernel, from one ncu capture of the configuration's plan (the summary
+# under profiles/ named for the kernel); reported only when a run uses that plan.
+TRAFFIC = {"fp64-32768": {"plan": (2048, 8192, 8192), "bytes": 2.624778e9 + 135.795456e6,
+                          "profile": "profiles/fp64_tile_kernel_traffic_32768.md"}}
 
 
 def parse():
@@ -76,6 +88,8 @@ def parse():
     ap.add_argument("--budget-gib", type=float, default=0.0)
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--form", default="", choices=["", "fp64", "ozaki"],
+                    help="GEMM form of the level-3 configurations' updates (default FP64)")
     return ap.parse_args()
 
 
@@ -335,11 +349,15 @@ def run_ours(args, w, world, rank, local, pg):
     s0 = stats[0][0]
     link_h2d, link_d2h = P.ooc_query_device()[1:]
     b_alg = s0.h2d_bytes + s0.d2h_bytes
+    tr = TRAFFIC.get(args.config)
+    traffic = tr["bytes"] if tr and not args.n and (s0.mb, s0.nb, s0.kb) == tr["plan"] else None
     if w["form"] == "fp64":
         peak = pk["bf16_tflops_sustained"] * NOMINAL_FP64_TF / NOMINAL_BF16_TF
         achieved = flops * args.steps / ker_s / 1e12
         roof = {"bound": "tensor", "kernel": "fp64_tile_kernel (FP64 mma.sync, TMA-fed)",
-                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                "traffic_alg_bytes": 8.0 * (s0.mb * s0.kb + s0.kb * s0.nb + 2 * s0.mb * s0.nb),
+                "traffic_source": tr["profile"] if traffic else None,
                 "peak_source": "%s bf16 sustained %.1f TF x nominal FP64/BF16 ratio %.2f/%.0f" % (
                     pk_src, pk["bf16_tflops_sustained"], NOMINAL_FP64_TF, NOMINAL_BF16_TF),
                 "fp64_cublas_measured_tflops": cublas_tf, "frac_of_cublas_dgemm": achieved / cublas_tf,
@@ -524,12 +542,260 @@ def run_batched_bench(args, w, world, rank, local, pg):
     print(json.dumps(line), flush=True)
 
 
+def level3_flops(w):
+    n = w["M"]
+    if w["form"] == "syrk":
+        return float(n) * (n + 1) * w["K"]
+    if w["form"] == "trsm":
+        return float(n) * n * w["N"]
+    return float(n) ** 3 / 3.0
+
+
+def level3_inputs(w, rank, torch):
+    """Pinned host operands of a level-3 configuration (and pristine copies of what the call overwrites)."""
+    n, N, K = w["M"], w["N"], w["K"]
+    seed = 300 + rank
+    if w["form"] == "syrk":
+        A = torch.empty((n, K), dtype=torch.float64, pin_memory=True)
+        C = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
+        synth.fill(A, seed, 0, w["dist"])
+        synth.fill(C, seed, 2, w["dist"])
+        return dict(A=A, C=C)
+    if w["form"] == "trsm":
+        # lower triangular, diagonally dominant: off-diagonal U[-1,1] / n, diagonal 2 (well conditioned)
+        A = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
+        synth.fill(A, seed, 0, w["dist"])
+        a = A.numpy()
+        for r0 in range(0, n, 4096):   # row strips: bounded temporary memory
+            blk = a[r0:r0 + 4096]
+            blk *= 1.0 / n
+            blk[:, r0 + 4096:] = 0.0
+            for i in range(blk.shape[0]):
+                blk[i, r0 + i + 1:] = 0.0
+                blk[i, r0 + i] = 2.0
+        B = torch.empty((n, N), dtype=torch.float64, pin_memory=True)
+        synth.fill(B, seed, 1, synth.NORMAL)
+        B0 = torch.empty_like(B, pin_memory=True)
+        B0.copy_(B)
+        return dict(A=A, B=B, B0=B0)
+    # potrf: symmetric N(0,1) off the diagonal (lower triangle read), diagonal n + N(0,1): SPD, well conditioned
+    A = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
+    synth.fill(A, seed, 0, w["dist"])
+    a = A.numpy()
+    a[np.diag_indices(n)] += float(n)
+    A0 = torch.empty_like(A, pin_memory=True)
+    A0.copy_(A)
+    return dict(A=A, A0=A0)
+
+
+def level3_call(P, w, ops, opts, st):
+    n, N, K = w["M"], w["N"], w["K"]
+    if w["form"] == "syrk":
+        return P.ooc_dsyrk("L", "N", n, K, w["alpha"], ops["A"], K, w["beta"], ops["C"], n, w["budget"], opts, st), 0
+    if w["form"] == "trsm":
+        return P.ooc_dtrsm("L", "L", "N", "N", n, N, w["alpha"], ops["A"], n, ops["B"], N, w["budget"], opts, st), 0
+    return P.ooc_dpotrf("L", n, ops["A"], n, w["budget"], opts, st)
+
+
+def level3_restore(w, ops):
+    """Put back what the previous call overwrote (outside the timed region)."""
+    if w["form"] == "trsm":
+        ops["B"].copy_(ops["B0"])
+    elif w["form"] == "potrf":
+        ops["A"].copy_(ops["A0"])
+
+
+def level3_parity(w, ops, before, cores):
+    """Oracle check of the last call on a bounded sample; returns (parity dict, cpu_baseline dict)."""
+    from oracle import level3 as L3
+    import oracle
+    n, N, K = w["M"], w["N"], w["K"]
+    tol = FORMS[w["form"]][1]
+    if w["form"] == "syrk":
+        r = 64
+        t0 = time.perf_counter()
+        errs = []
+        for (i, j), c0 in before:
+            ref = L3.syrk_block("L", "N", i, j, r, r, w["alpha"], ops["A"].numpy(), w["beta"], c0, nthreads=cores)
+            errs.append(oracle.rel_fro(ops["C"].numpy()[i:i + r, j:j + r][L3.tri_mask(r, r, "L", 0, i, j)],
+                                       ref[L3.tri_mask(r, r, "L", 0, i, j)]))
+        dt = time.perf_counter() - t0
+        flops = 2.0 * r * r * K * len(before)
+        sample = "%d seeded %dx%d blocks of the lower triangle, K=%d" % (len(before), r, r, K)
+    elif w["form"] == "trsm":
+        cols = before["cols"]
+        t0 = time.perf_counter()
+        ref = L3.trsm("L", "L", "N", "N", w["alpha"], ops["A"].numpy(), before["B0"], nthreads=cores)
+        dt = time.perf_counter() - t0
+        got = ops["B"].numpy()[:, cols]
+        errs = [oracle.rel_fro(got, ref)]
+        flops = float(n) * n * len(cols)
+        sample = "%d seeded right-hand sides (columns of B) of order %d" % (len(cols), n)
+    else:
+        b = before["lead"]
+        t0 = time.perf_counter()
+        ref, info = L3.potrf("L", before["A0lead"], nthreads=cores)
+        dt = time.perf_counter() - t0
+        m = L3.tri_mask(b, b, "L")
+        errs = [oracle.rel_fro(ops["A"].numpy()[:b, :b][m], ref[m])]
+        # sampled entries of L L^T against the input, anywhere in the matrix
+        a = ops["A"].numpy()
+        worst = 0.0
+        for (i, j), aij in before["entries"]:
+            k = min(i, j) + 1
+            llt = float(np.dot(a[i, :k], a[j, :k]))
+            worst = max(worst, abs(llt - aij) / float(n))
+        errs.append(worst)
+        flops = float(b) ** 3 / 3.0
+        sample = "leading %dx%d block factored by the oracle; %d sampled entries of L L^T" % (
+            b, b, len(before["entries"]))
+    parity = {"max_rel_fro": max(errs), "tolerance": tol, "pass": max(errs) <= tol}
+    cpu = {"value": flops / dt / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+           "sample": sample + ", %.1f s" % dt}
+    return parity, cpu
+
+
+def level3_snapshot(w, ops):
+    """What the oracle check needs from the inputs of the next call."""
+    n, N = w["M"], w["N"]
+    rng = np.random.default_rng(4321)
+    if w["form"] == "syrk":
+        r = 64
+        out = []
+        for _ in range(12):
+            i = int(rng.integers(0, n - r + 1))
+            j = int(rng.integers(0, i + 1)) if i > 0 else 0
+            out.append(((i, j), ops["C"].numpy()[i:i + r, j:j + r].copy()))
+        out.append(((0, 0), ops["C"].numpy()[:r, :r].copy()))
+        out.append(((n - r, n - r), ops["C"].numpy()[n - r:, n - r:].copy()))
+        return out
+    if w["form"] == "trsm":
+        cols = sorted(set(int(c) for c in rng.integers(0, N, size=6)) | {0, N - 1})
+        return {"cols": cols, "B0": ops["B"].numpy()[:, cols].copy()}
+    b = min(n, 2048)
+    ents = []
+    for _ in range(64):
+        i = int(rng.integers(0, n))
+        j = int(rng.integers(0, i + 1))
+        ents.append(((i, j), float(ops["A"].numpy()[i, j])))
+    return {"lead": b, "A0lead": ops["A"].numpy()[:b, :b].copy(), "entries": ents}
+
+
+def run_level3_bench(args, w, world, rank, local, pg):
+    """SYRK / TRSM / Cholesky configurations: one driver call per step."""
+    import torch
+    cores = host_cores()
+    flops = level3_flops(w)
+    metric = "out-of-core %s effective TFLOP/s incl. transfers" % w["form"].upper()
+    desc = {"syrk": "SYRK C = A A^T (lower) N=%d K=%d, alpha=%g beta=%g, N(0,1)" % (w["M"], w["K"], w["alpha"],
+                                                                                   w["beta"]),
+            "trsm": "TRSM L X = B, lower non-unit, M=%d N=%d, diagonally dominant" % (w["M"], w["N"]),
+            "potrf": "Cholesky A = L L^T N=%d, SPD (symmetric N(0,1) + N I)" % w["M"]}[w["form"]]
+    cfg = {"workload": "out-of-core " + desc + ", device budget %.2f GiB" % (w["budget"] / 2 ** 30),
+           "form": w["form"], "update_form": args.form or "fp64", "device_budget_bytes": w["budget"],
+           "l2": "inputs larger than L2: host operands of %d GiB streamed through the device budget" % (
+               (8 * w["M"] * (w["M"] + max(w["N"], w["K"]))) >> 30)}
+    import torch
+    ops = level3_inputs(w, rank, torch)
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        times = []
+        for it in range(args.warmup + args.steps):
+            snap = level3_snapshot(w, ops)
+            par, cpu = level3_parity(w, ops, snap, cores)   # the oracle on the sample (parity is vacuous here)
+            if it >= args.warmup:
+                times.append(cpu)
+        value = sum(c["value"] for c in times) / len(times)
+        line = {"impl": "reference", "metric": metric, "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Philox)",
+                "config": cfg, "cpu_baseline": dict(times[-1], value=value),
+                "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+    import paper_1808_05056_gb300 as P
+    torch.cuda.set_device(local)
+    P.load()
+    opts = P.make_opts(form=P.OOC_FORM_OZAKI if args.form == "ozaki" else P.OOC_FORM_FP64)
+
+    def step():
+        st = P.ooc_stats()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, info = level3_call(P, w, ops, opts, st)
+        wall = time.perf_counter() - t0
+        if rc != 0 or info != 0:
+            raise RuntimeError("%s failed: %s (info %d): %s" % (w["form"], P.ooc_strerror(rc), info,
+                                                                P.ooc_last_error()))
+        return st, wall
+
+    for k in range(max(0, args.warmup - 1)):
+        step()
+        level3_restore(w, ops)
+    snap = level3_snapshot(w, ops) if rank == 0 else None
+    step()
+    parity = cpu = None
+    if rank == 0:
+        parity, cpu = level3_parity(w, ops, snap, cores)
+    level3_restore(w, ops)
+    clk = ClockSampler(local, enabled=not args.no_clocks)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    stats = []
+    for k in range(args.steps):
+        stats.append(step())
+        if k + 1 < args.steps:
+            level3_restore(w, ops)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    clocks = clk.stop()
+    wall_s = sum(wl for _, wl in stats)
+    ker_s = sum(s.kernel_seconds for s, _ in stats)
+    if pg:
+        import torch.distributed as dist
+        t = torch.tensor([wall_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        wall_s = t.item()
+    if rank != 0:
+        return
+    s0 = stats[0][0]
+    value = world * flops * args.steps / wall_s / 1e12
+    pk, pk_src = peaks()
+    compute_peak = (pk["bf16_tflops_sustained"] * NOMINAL_FP64_TF / NOMINAL_BF16_TF if args.form != "ozaki"
+                    else pk["bf16_tflops_sustained"] / 36.0)
+    t_roof = flops / (compute_peak * 1e12)
+    line = {
+        "metric": metric, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * wall_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Philox, pinned host)",
+        "config": cfg,
+        "roofline": {"bound": "tensor", "kernel": "pipelined out-of-core GEMM updates (%s tile kernel)" % (
+                         "tc_terms Ozaki" if args.form == "ozaki" else "fp64_tile"),
+                     "achieved": flops * args.steps / wall_s / 1e12, "peak": compute_peak, "unit": "TFLOP/s",
+                     "frac": t_roof * args.steps / wall_s, "traffic": None,
+                     "peak_source": "%s bf16 sustained %.1f TF x %s" % (
+                         pk_src, pk["bf16_tflops_sustained"],
+                         "nominal FP64/BF16 ratio" if args.form != "ozaki" else "1/36 Ozaki products")},
+        "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": s0.h2d_bytes,
+                "d2h_bytes_per_step": s0.d2h_bytes},
+        "gpu_launches": s0.kernel_launches,
+        "gemm_calls_per_step": s0.steps, "kernel_seconds_per_step": ker_s / args.steps,
+        "parity": parity, "cpu_baseline": cpu, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     w = workload(args)
     world, rank, local, pg = dist_init(args)
     args.gpus = world if world > 1 else args.gpus
-    if w["form"] == "batched":
+    if w["form"] in LEVEL3:
+        run_level3_bench(args, w, world, rank, local, pg)
+    elif w["form"] == "batched":
         run_batched_bench(args, w, world, rank, local, pg)
     elif args.impl == "reference":
         run_reference(args, w, world, rank, pg)
