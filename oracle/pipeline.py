@@ -19,8 +19,10 @@ CUDA stream semantics: operations of one stream run in issue order; a wait on
 event E orders every later operation of its stream after everything issued on
 the recording stream before the most recent record of E issued earlier.
 
-check(schedule) returns a list of violation strings (empty when the rule holds
-for every execution the stream/event order allows):
+check(schedule, initial) returns a list of violation strings (empty when the
+rule holds for every execution the stream/event order allows); `initial` lists
+slot contents left on the device by an earlier call (Section IV's nsteps
+invocations, where C blocks stay resident between calls):
   * a read is not preceded (happens-before) by a write of the expected tag to
     that slot, or another write to the slot may fall between them;
   * two writes of one slot are unordered;
@@ -57,10 +59,18 @@ def _hb(a, b):
     return all(x <= y for x, y in zip(a, b)) and a != b
 
 
-def check(schedule):
-    clocks = _vector_clocks(schedule)
+def check(schedule, initial=()):
+    """initial: (slot, tag) pairs held by device slots before the schedule
+    starts (data a previous call left resident); they happen before every op."""
+    raw = _vector_clocks(schedule)
+    zero = [0] * (len(raw[0]) if raw else 0)
+
+    class _Clocks:
+        def __getitem__(self, pos):
+            return zero if pos < 0 else raw[pos]
+    clocks = _Clocks()
     violations = []
-    writes = {}   # slot -> list of (pos, tag)
+    writes = {slot: [(-1, tag)] for slot, tag in initial}   # slot -> list of (pos, tag)
     reads = {}    # slot -> list of (pos, tag)
     for pos, op in enumerate(schedule):
         for slot, tag in op.get("writes", []):

@@ -98,3 +98,20 @@ def test_checker_unordered_streams_and_stale_event():
            dict(kind="kernel", stream=1, reads=[("X", 2)]),
            dict(kind="record", stream=0, event="e")]
     assert pipeline.check(ops)
+
+
+def test_resident_content_from_an_earlier_call():
+    """A slot left on the device by an earlier call (nsteps mode) may be read without a
+    load in this call only when declared as initial content with the matching tag."""
+    sched = [
+        dict(kind="h2d", stream=0, writes=[(0, ("A", 0))], reads=[]),
+        dict(kind="record", stream=0, event=0),
+        dict(kind="wait", stream=1, event=0),
+        dict(kind="kernel", stream=1, reads=[(0, ("A", 0)), (5, ("C", 0, 0, 1))], writes=[(5, ("C", 0, 0, 2))]),
+    ]
+    assert pipeline.check(sched)                                   # nothing wrote slot 5
+    assert pipeline.check(sched, initial=[(5, ("C", 0, 0, 1))]) == []
+    assert pipeline.check(sched, initial=[(5, ("C", 0, 0, 0))])    # stale version
+    # a later load into the resident slot must still be ordered after the kernel's read
+    bad = sched + [dict(kind="h2d", stream=0, writes=[(5, ("C", 1, 0, 0))], reads=[])]
+    assert pipeline.check(bad, initial=[(5, ("C", 0, 0, 1))])
