@@ -263,6 +263,46 @@ int ooc_dtrsm(char side, char uplo, char transA, char diag, int64_t M, int64_t N
 int ooc_dpotrf(char uplo, int64_t N, double* A, int64_t lda, size_t device_budget_bytes,
                const ooc_opts* opts, ooc_stats* stats, int64_t* info);
 
+/* ---- sessions: one C over several calls (Section IV's nsteps) ------------ */
+/*
+ * Section IV gives the out-of-core DGEMM an nsteps parameter: it can be the
+ * per-step update of SUMMA or hierarchical SUMMA, called once per main step
+ * with that step's panels, all steps adding into one C (the paper keeps the
+ * C blocks of its two C buffers on the device between calls).  A session does
+ * this for an M x N C: it fixes the C blocking and keeps as many C blocks as
+ * fit in HBM across the calls; the other blocks travel to the host and back in
+ * every call.  On GB300 a 32 GiB C fits whole.
+ *
+ * ooc_session_create: C (pinned, M x N, ldc >= N) is the result matrix and the
+ *   initial value; the final result is beta * C + sum of the calls' products.
+ *   k_hint (0: 4096) is the largest inner dimension a call is planned for: the
+ *   resident blocks are chosen so that a call of that K still streams its
+ *   operands beside them (FP64 calls with a larger K stream it in chunks;
+ *   Ozaki calls then fail with OOC_ERR_BUDGET).  opts->form: FP64 or Ozaki;
+ *   opts->workspace (holding the budget) makes the session allocate nothing.
+ *   The session owns one arena of device_budget_bytes and three streams.
+ * ooc_session_step: adds alpha * op(A) * op(B) (op(A) M x K, op(B) K x N,
+ *   layouts as for ooc_dgemm) into the session's C; synchronous, A and B may
+ *   be reused when it returns.  The first call also applies beta (beta == 0
+ *   never reads C).  Until ooc_session_finish the host C holds partial sums
+ *   for streamed blocks and stale values for resident ones, and must not be
+ *   changed by the caller.
+ * ooc_session_finish: writes the resident blocks back (after a call with
+ *   K = 0 when no step was made, so C = beta * C) and destroys the session;
+ *   stats (nullable): totals since creation, tflops over 2 M N sum(K).
+ * ooc_session_free: destroys a session without writing anything back.
+ * ooc_session_query: the blocking, how many of its blocks are resident, calls.
+ */
+typedef struct ooc_session ooc_session;
+int ooc_session_create(int64_t M, int64_t N, int64_t k_hint, double beta, double* C, int64_t ldc,
+                       size_t device_budget_bytes, const ooc_opts* opts, ooc_session** session);
+int ooc_session_step(ooc_session* session, char transA, char transB, int64_t K, double alpha,
+                     const double* A, int64_t lda, const double* B, int64_t ldb, ooc_stats* stats);
+int ooc_session_finish(ooc_session* session, ooc_stats* stats);
+int ooc_session_free(ooc_session* session);
+int ooc_session_query(const ooc_session* session, int64_t* mb, int64_t* nb, int64_t* resident_blocks,
+                      int64_t* blocks, int32_t* calls);
+
 /*
  * Plan only (host, no device needed): the block/chunk/buffer plan the call
  * with these arguments would use.  elem_bytes is 8 for ooc_dgemm, 4 for
@@ -308,6 +348,18 @@ int ooc_schedule(int64_t M, int64_t N, int64_t K, int32_t elem_bytes, int32_t be
 int ooc_schedule_gemmt(char uplo, int64_t N, int64_t K, int32_t elem_bytes, int32_t beta_nonzero,
                        size_t device_budget_bytes, const ooc_opts* opts, ooc_stats* plan,
                        ooc_sched_op* out, int64_t capacity, int64_t* count);
+
+/*
+ * Export the schedule of one session call (host only): FP64 operands, the
+ * blocking forced by opts->mb / opts->nb, the first resident_blocks updated
+ * blocks resident, call 0 (applies beta) or a later call (call > 0: resident
+ * blocks start from their slot contents and are not copied back; streamed
+ * blocks bring their partial sums from the host).  As ooc_schedule_gemmt.
+ */
+int ooc_schedule_session(int64_t M, int64_t N, int64_t K, int32_t beta_nonzero,
+                         size_t device_budget_bytes, const ooc_opts* opts, int32_t resident_blocks,
+                         int32_t call, ooc_stats* plan, ooc_sched_op* out, int64_t capacity,
+                         int64_t* count);
 
 /* ---- plan search: candidates, autotuner, learned cost model ------------ */
 /* The paper has no plan search beyond its partitioner (Section IV); these

@@ -126,13 +126,23 @@ def load(path=None):
                                        ctypes.POINTER(i64)]
     lib.ooc_dtrsm.argtypes = [ch, ch, ch, ch, i64, i64, dbl, vp, i64, vp, i64, sz, po, ps]
     lib.ooc_dpotrf.argtypes = [ch, i64, vp, i64, sz, po, ps, ctypes.POINTER(i64)]
+    sp = ctypes.c_void_p
+    lib.ooc_session_create.argtypes = [i64, i64, i64, dbl, vp, i64, sz, po, ctypes.POINTER(sp)]
+    lib.ooc_session_step.argtypes = [sp, ch, ch, i64, dbl, vp, i64, vp, i64, ps]
+    lib.ooc_session_finish.argtypes = [sp, ps]
+    lib.ooc_session_free.argtypes = [sp]
+    lib.ooc_session_query.argtypes = [sp] + [ctypes.POINTER(i64)] * 4 + [ctypes.POINTER(i32)]
+    lib.ooc_schedule_session.argtypes = [i64, i64, i64, i32, sz, po, i32, i32, ps, ctypes.POINTER(ooc_sched_op),
+                                         i64, ctypes.POINTER(i64)]
     lib.ooc_query_device.argtypes = [ctypes.POINTER(sz), ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
     lib.ooc_strerror.argtypes = [ctypes.c_int]
     lib.ooc_strerror.restype = ctypes.c_char_p
     lib.ooc_last_error.argtypes = []
     lib.ooc_last_error.restype = ctypes.c_char_p
     for f in ("ooc_dgemm", "ooc_sgemm", "ooc_dgemm_device", "ooc_plan", "ooc_schedule", "ooc_query_device",
-              "ooc_dgemmt", "ooc_dsyrk", "ooc_ssyrk", "ooc_schedule_gemmt", "ooc_dtrsm", "ooc_dpotrf"):
+              "ooc_dgemmt", "ooc_dsyrk", "ooc_ssyrk", "ooc_schedule_gemmt", "ooc_dtrsm", "ooc_dpotrf",
+              "ooc_session_create", "ooc_session_step", "ooc_session_finish", "ooc_session_free",
+              "ooc_session_query", "ooc_schedule_session"):
         getattr(lib, f).restype = ctypes.c_int
     if path is None:
         _lib = lib
@@ -227,6 +237,44 @@ def ooc_dpotrf(uplo, N, A, lda, budget, opts=None, stats=None):
     info = ctypes.c_int64(0)
     rc = load().ooc_dpotrf(uplo.encode(), N, _ptr(A), lda, budget, _ref(opts), _ref(stats), ctypes.byref(info))
     return rc, info.value
+
+
+class Session:
+    """A C-ABI session (ooc_session_*): one C accumulated over several calls."""
+
+    def __init__(self, M, N, C, ldc, beta, budget, k_hint=0, opts=None):
+        self._h = ctypes.c_void_p()
+        self.rc = load().ooc_session_create(M, N, k_hint, beta, _ptr(C), ldc, budget, _ref(opts),
+                                            ctypes.byref(self._h))
+
+    def step(self, transA, transB, K, alpha, A, lda, B, ldb, stats=None):
+        return load().ooc_session_step(self._h, transA.encode(), transB.encode(), K, alpha, _ptr(A), lda, _ptr(B),
+                                       ldb, _ref(stats))
+
+    def query(self):
+        v = [ctypes.c_int64() for _ in range(4)] + [ctypes.c_int32()]
+        _check(load().ooc_session_query(self._h, *[ctypes.byref(x) for x in v]), "ooc_session_query")
+        return dict(mb=v[0].value, nb=v[1].value, resident_blocks=v[2].value, blocks=v[3].value, calls=v[4].value)
+
+    def finish(self, stats=None):
+        h, self._h = self._h, ctypes.c_void_p()
+        return load().ooc_session_finish(h, _ref(stats))
+
+    def free(self):
+        if self._h:
+            load().ooc_session_free(self._h)
+            self._h = ctypes.c_void_p()
+
+
+def ooc_schedule_session(M, N, K, beta_nonzero, budget, opts, resident_blocks, call):
+    """C ABI ooc_schedule_session; returns (plan dict, list of operation dicts)."""
+    lib = load()
+    st = ooc_stats()
+    o = _ref(opts)
+    ops = _export(lambda buf, cap, n: lib.ooc_schedule_session(M, N, K, int(bool(beta_nonzero)), budget, o,
+                                                               resident_blocks, call, ctypes.byref(st), buf, cap, n),
+                  "ooc_schedule_session")
+    return st.as_dict(), ops
 
 
 def ooc_dgemm_batched(descs, budget, opts=None, stats=None):

@@ -17,6 +17,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -255,6 +256,7 @@ struct Exec {
     char* arena = nullptr;     // device arena; its first word is the launch error word
     char* base = nullptr;      // base of the current plan's slot region inside the arena
     bool own_arena = false;
+    bool own_streams = true;   // false: the streams belong to a session and outlive this call
     cudaStream_t st[3] = {nullptr, nullptr, nullptr};
     cudaStream_t extra_compute = nullptr;  // second compute stream (batched calls)
     cudaStream_t smap[3] = {nullptr, nullptr, nullptr};  // schedule stream id -> stream for the current plan
@@ -287,7 +289,7 @@ struct Exec {
         t_begin = nullptr;
         for (auto& e : t_end) { if (e) cudaEventDestroy(e); e = nullptr; }
         if (extra_compute) cudaStreamSynchronize(extra_compute);
-        for (auto& s : st) { if (s) cudaStreamDestroy(s); s = nullptr; }
+        for (auto& s : st) { if (s && own_streams) cudaStreamDestroy(s); s = nullptr; }
         if (extra_compute) cudaStreamDestroy(extra_compute);
         extra_compute = nullptr;
         if (own_arena && arena) cudaFree(arena);
@@ -513,6 +515,88 @@ int issue_ops(Exec& x, const Plan& p, const std::vector<Op>& ops, const Operands
     return OOC_OK;
 }
 
+// Issue a planned schedule on x's streams (already created) and arena, wait for
+// it, check the device error word and fill the device-side statistics (the
+// caller sets seconds / tflops after releasing its resources).
+int execute(Exec& x, const std::vector<Op>& ops, const Operands& o, int es, const Inject& inj, ooc_stats* stats)
+{
+    const Plan& p = x.p;
+    std::string why;
+    int rc = OOC_OK;
+    x.gen.assign(p.slots(), 0);
+    x.split_gen.assign(p.slots(), -1);
+    x.ev.resize(n_events(p), nullptr);
+    for (auto& e : x.ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    int64_t nkern = 0;
+    for (const Op& op : ops) nkern += op.kind == kKernel;
+    x.kev.resize(2 * nkern, nullptr);
+    for (auto& e : x.kev) CK(cudaEventCreate(&e));
+    CK(cudaEventCreate(&x.t_begin));
+    for (auto& e : x.t_end) CK(cudaEventCreate(&e));
+
+    int* err = reinterpret_cast<int*>(x.arena);
+    CK(cudaEventRecord(x.t_begin, x.st[kStreamH2D]));
+    CK(cudaStreamWaitEvent(x.st[kStreamCompute], x.t_begin, 0));
+    CK(cudaStreamWaitEvent(x.st[kStreamD2H], x.t_begin, 0));
+    CK(cudaMemsetAsync(err, 0, sizeof(int), x.st[kStreamCompute]));
+
+    x.base = x.arena;
+    x.smap[0] = x.st[0]; x.smap[1] = x.st[1]; x.smap[2] = x.st[2];
+    x.ev_base = 0;
+    rc = issue_ops(x, p, ops, o, es, inj, why);
+    if (rc) return rc;
+    const char* trace_path = std::getenv("OOC_TRACE");
+    for (int i = 0; i < 3; ++i) CK(cudaEventRecord(x.t_end[i], x.st[i]));
+    for (auto s : x.st) CK(cudaStreamSynchronize(s));
+    int herr = 0;
+    CK(cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (herr != 0) return fail(OOC_ERR_TIMEOUT, "a device-side wait gave up (status " + std::to_string(herr) + ")");
+    if (trace_path) {
+        if (FILE* f = std::fopen(trace_path, "a")) {
+            std::fprintf(f, "# call M=%lld N=%lld K=%lld mb=%lld nb=%lld kb=%lld nA=%d nB=%d nC=%d\n", (long long)p.M,
+                         (long long)p.N, (long long)p.K, (long long)p.mb, (long long)p.nb, (long long)p.kb, p.nA, p.nB,
+                         p.nC);
+            double prev = 0;
+            for (auto& r : x.trace) {
+                float a = 0, b = 0;
+                cudaEventElapsedTime(&a, x.t_begin, r.e0);
+                cudaEventElapsedTime(&b, x.t_begin, r.e1);
+                const char* k = r.kind == kH2D ? "h2d" : r.kind == kKernel ? "kernel" : "d2h";
+                std::fprintf(f, "%s,%d,%lld,%lld,%lld,%.0f,%.3f,%.3f,%.3f\n", k, r.stream, (long long)r.i,
+                             (long long)r.j, (long long)r.kc, r.bytes - prev, r.host_ms, a, b);
+                prev = r.bytes;
+            }
+            std::fclose(f);
+        }
+    }
+
+    if (stats) {
+        float ms = 0, best = 0;
+        for (auto e : x.t_end) {
+            CK(cudaEventElapsedTime(&ms, x.t_begin, e));
+            best = std::max(best, ms);
+        }
+        double ksum = 0;
+        for (int64_t k = 0; k < x.n_kern; ++k) {
+            CK(cudaEventElapsedTime(&ms, x.kev[2 * k], x.kev[2 * k + 1]));
+            ksum += ms;
+        }
+        stats->device_seconds = best * 1e-3;
+        stats->kernel_seconds = ksum * 1e-3;
+        stats->h2d_bytes = x.h2d;
+        stats->d2h_bytes = x.d2h;
+        stats->mb = p.mb; stats->nb = p.nb; stats->kb = p.kb;
+        stats->depth = p.nA; stats->c_buffers = p.nC; stats->b_buffers = p.nB; stats->form = p.form;
+        int64_t nblk = 0;
+        for (const Op& op : ops) nblk += op.kind == kD2H;
+        stats->blocks = nblk; stats->steps = x.n_kern;
+        stats->device_bytes = (int64_t)p.device_bytes;
+        stats->slices = p.slices; stats->products = p.products;
+        stats->kernel_launches = x.launches;
+    }
+    return OOC_OK;
+}
+
 // tri / tri_off: triangular update of C (Plan::tri); 0 updates all of C.
 int run_ooc(char ta, char tb, int64_t M, int64_t N, int64_t K, const Operands& o, int es, size_t budget,
             const ooc_opts* opts_in, ooc_stats* stats, int tri = 0, int64_t tri_off = 0)
@@ -563,83 +647,14 @@ int run_ooc(char ta, char tb, int64_t M, int64_t N, int64_t K, const Operands& o
         x.own_arena = true;
     }
     for (auto& s : x.st) CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
-    x.gen.assign(p.slots(), 0);
-    x.split_gen.assign(p.slots(), -1);
-    x.ev.resize(n_events(p), nullptr);
-    for (auto& e : x.ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-    int64_t nkern = 0;
-    for (const Op& op : ops) nkern += op.kind == kKernel;
-    x.kev.resize(2 * nkern, nullptr);
-    for (auto& e : x.kev) CK(cudaEventCreate(&e));
-    CK(cudaEventCreate(&x.t_begin));
-    for (auto& e : x.t_end) CK(cudaEventCreate(&e));
-
-    int* err = reinterpret_cast<int*>(x.arena);
-    CK(cudaEventRecord(x.t_begin, x.st[kStreamH2D]));
-    CK(cudaStreamWaitEvent(x.st[kStreamCompute], x.t_begin, 0));
-    CK(cudaStreamWaitEvent(x.st[kStreamD2H], x.t_begin, 0));
-    CK(cudaMemsetAsync(err, 0, sizeof(int), x.st[kStreamCompute]));
-
-    x.base = x.arena;
-    x.smap[0] = x.st[0]; x.smap[1] = x.st[1]; x.smap[2] = x.st[2];
-    x.ev_base = 0;
-    rc = issue_ops(x, p, ops, o, es, inj, why);
+    // a triangular update of a square C counts N (N + 1) K flops (the level-3 BLAS convention for SYRK)
+    const double flops = tri ? (double)M * (M + 1) * K : 2.0 * (double)M * N * K;
+    rc = execute(x, ops, o, es, inj, stats);
     if (rc) return rc;
-    const char* trace_path = std::getenv("OOC_TRACE");
-    for (int i = 0; i < 3; ++i) CK(cudaEventRecord(x.t_end[i], x.st[i]));
-    for (auto s : x.st) CK(cudaStreamSynchronize(s));
-    int herr = 0;
-    CK(cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (herr != 0) return fail(OOC_ERR_TIMEOUT, "a device-side wait gave up (status " + std::to_string(herr) + ")");
-    if (trace_path) {
-        if (FILE* f = std::fopen(trace_path, "a")) {
-            std::fprintf(f, "# call M=%lld N=%lld K=%lld mb=%lld nb=%lld kb=%lld nA=%d nB=%d nC=%d\n", (long long)M,
-                         (long long)N, (long long)K, (long long)p.mb, (long long)p.nb, (long long)p.kb, p.nA, p.nB,
-                         p.nC);
-            double prev = 0;
-            for (auto& r : x.trace) {
-                float a = 0, b = 0;
-                cudaEventElapsedTime(&a, x.t_begin, r.e0);
-                cudaEventElapsedTime(&b, x.t_begin, r.e1);
-                const char* k = r.kind == kH2D ? "h2d" : r.kind == kKernel ? "kernel" : "d2h";
-                std::fprintf(f, "%s,%d,%lld,%lld,%lld,%.0f,%.3f,%.3f,%.3f\n", k, r.stream, (long long)r.i,
-                             (long long)r.j, (long long)r.kc, r.bytes - prev, r.host_ms, a, b);
-                prev = r.bytes;
-            }
-            std::fclose(f);
-        }
-    }
-
-    if (stats) {
-        float ms = 0, best = 0;
-        for (auto e : x.t_end) {
-            CK(cudaEventElapsedTime(&ms, x.t_begin, e));
-            best = std::max(best, ms);
-        }
-        double ksum = 0;
-        for (int64_t k = 0; k < x.n_kern; ++k) {
-            CK(cudaEventElapsedTime(&ms, x.kev[2 * k], x.kev[2 * k + 1]));
-            ksum += ms;
-        }
-        stats->device_seconds = best * 1e-3;
-        stats->kernel_seconds = ksum * 1e-3;
-        stats->h2d_bytes = x.h2d;
-        stats->d2h_bytes = x.d2h;
-        stats->mb = p.mb; stats->nb = p.nb; stats->kb = p.kb;
-        stats->depth = p.nA; stats->c_buffers = p.nC; stats->b_buffers = p.nB; stats->form = p.form;
-        int64_t nblk = 0;
-        for (const Op& op : ops) nblk += op.kind == kD2H;
-        stats->blocks = nblk; stats->steps = x.n_kern;
-        stats->device_bytes = (int64_t)p.device_bytes;
-        stats->slices = p.slices; stats->products = p.products;
-        stats->kernel_launches = x.launches;
-    }
     // release before taking the wall time (the arena free is part of the call)
     x.release();
     if (stats) {
         stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_host0).count();
-        // a triangular update of a square C counts N (N + 1) K flops (the level-3 BLAS convention for SYRK)
-        const double flops = tri ? (double)M * (M + 1) * K : 2.0 * (double)M * N * K;
         stats->tflops = stats->seconds > 0 ? flops / stats->seconds / 1e12 : 0.0;
     }
     return OOC_OK;
@@ -1186,3 +1201,267 @@ int ooc_dgemm_device(char transA, char transB, int64_t M, int64_t N, int64_t K, 
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ session --
+// Section IV's nsteps mode: the out-of-core GEMM called once per step of an
+// outer algorithm (SUMMA and its hierarchical form), all calls adding into one
+// C.  The session fixes the C blocking, keeps as many C blocks as the budget
+// allows in HBM across the calls (the paper keeps the last two blocks of its
+// pair of C buffers back between calls), and writes them back at the end.
+struct ooc_session {
+    int64_t M = 0, N = 0;
+    double* C = nullptr;
+    int64_t ldc = 0;
+    double beta = 0.0;
+    size_t budget = 0;
+    ooc_opts opts{};
+    int64_t mb = 0, nb = 0, h = 0, w = 0;
+    int32_t nR = 0;
+    int32_t calls = 0;
+    char* arena = nullptr;
+    bool own_arena = false;
+    cudaStream_t st[3] = {nullptr, nullptr, nullptr};
+    size_t c_slot = 0, header = 256;
+    int64_t ldc_dev = 0;
+    double h2d = 0, d2h = 0, kernel_s = 0, device_s = 0, flops = 0;
+    int64_t launches = 0, steps = 0;
+    std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+
+    ~ooc_session()
+    {
+        for (auto s : st)
+            if (s) {
+                cudaStreamSynchronize(s);
+                cudaStreamDestroy(s);
+            }
+        if (own_arena && arena) cudaFree(arena);
+        cudaGetLastError();
+    }
+};
+
+namespace {
+
+PlanRequest session_request(const ooc_session& s, char ta, char tb, int64_t K, int32_t nR, int32_t call)
+{
+    ooc_opts o = s.opts;
+    o.mb = s.mb;
+    o.nb = s.nb;
+    o.workspace = nullptr;
+    o.workspace_bytes = 0;
+    o.flags &= ~(OOC_PLAN_MODEL | OOC_PLAN_PAPER);
+    PlanRequest rq{s.M, s.N, K, 8, s.beta != 0.0, is_t(ta), is_t(tb), s.budget, o};
+    rq.nR = nR;
+    rq.session_step = call;
+    rq.ldc = s.ldc;
+    double hg = 0, dg = 0;
+    if (ooc_query_device(nullptr, &hg, &dg) == OOC_OK && hg > 0 && dg > 0) {
+        rq.h2d_gbps = hg;
+        rq.d2h_gbps = dg;
+    }
+    return rq;
+}
+
+}  // namespace
+
+int ooc_session_create(int64_t M, int64_t N, int64_t k_hint, double beta, double* C, int64_t ldc,
+                       size_t device_budget_bytes, const ooc_opts* opts, ooc_session** out)
+{
+    if (!out) return fail(OOC_ERR_INVALID_ARG, "null session pointer");
+    *out = nullptr;
+    if (M <= 0 || N <= 0 || k_hint < 0 || !C || ldc < N) return fail(OOC_ERR_INVALID_ARG, "bad C or dimensions");
+    std::string why;
+    int rc = check_device(why);
+    if (rc) return fail(rc, why);
+    if (!range_pinned(C, M, N, ldc, 8))
+        return fail(OOC_ERR_NOT_PINNED, "host operands must be page-locked (cudaHostAlloc / cudaHostRegister)");
+    std::unique_ptr<ooc_session> s(new ooc_session());
+    s->M = M; s->N = N; s->C = C; s->ldc = ldc; s->beta = beta; s->budget = device_budget_bytes;
+    if (opts) s->opts = *opts;
+    if (s->opts.form == OOC_FORM_AUTO) s->opts.form = OOC_FORM_FP64;
+    if (s->opts.form != OOC_FORM_FP64 && s->opts.form != OOC_FORM_OZAKI)
+        return fail(OOC_ERR_INVALID_ARG, "a session runs the FP64 or Ozaki form");
+    if (s->opts.workspace && s->opts.workspace_bytes < device_budget_bytes)
+        return fail(OOC_ERR_INVALID_ARG, "workspace smaller than the budget");
+    const int64_t k = k_hint > 0 ? k_hint : 4096;
+    // the C blocking: the planner's choice for one call of inner dimension k
+    {
+        ooc_opts o = s->opts;
+        o.workspace = nullptr;
+        o.workspace_bytes = 0;
+        PlanRequest rq{M, N, k, 8, true, false, false, device_budget_bytes, o};
+        rq.session_step = 1;
+        Plan p;
+        if ((rc = make_plan(rq, p, why))) return fail(rc, why);
+        s->mb = p.mb; s->nb = p.nb;
+    }
+    s->h = (M + s->mb - 1) / s->mb;
+    s->w = (N + s->nb - 1) / s->nb;
+    // as many resident blocks as fit beside the streaming rings of a call with inner dimension k
+    auto fits = [&](int64_t r) {
+        Plan p;
+        std::string w2;
+        return make_plan(session_request(*s, 'N', 'N', k, (int32_t)r, 1), p, w2) == OOC_OK;
+    };
+    const int64_t blocks = s->h * s->w;
+    int64_t nR = 0;
+    if (blocks <= (1 << 30) && fits(blocks)) nR = blocks;
+    else {
+        int64_t lo = 0, hi = std::min<int64_t>(blocks - 1, 1 << 30);
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) / 2;
+            if (fits(mid)) lo = mid;
+            else hi = mid - 1;
+        }
+        nR = lo;
+    }
+    s->nR = (int32_t)nR;
+    if (s->opts.workspace) {
+        s->arena = static_cast<char*>(s->opts.workspace);
+    } else {
+        if (cudaMalloc(&s->arena, device_budget_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            s->arena = nullptr;
+            return fail(OOC_ERR_ALLOC, "device arena of " + std::to_string(device_budget_bytes) + " bytes");
+        }
+        s->own_arena = true;
+    }
+    for (auto& st : s->st)
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess)
+            return fail(OOC_ERR_CUDA, "stream creation failed");
+    *out = s.release();
+    return OOC_OK;
+}
+
+int ooc_session_step(ooc_session* s, char transA, char transB, int64_t K, double alpha, const double* A, int64_t lda,
+                     const double* B, int64_t ldb, ooc_stats* stats)
+{
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    if (!s) return fail(OOC_ERR_INVALID_ARG, "null session");
+    const auto t_host0 = std::chrono::steady_clock::now();
+    std::string why;
+    int rc = validate(transA, transB, s->M, s->N, K, A, lda, B, ldb, s->C, s->ldc, true, why);
+    if (rc) return fail(rc, why);
+    if (K == 0 && s->calls > 0) return OOC_OK;  // adds nothing
+    if (K > 0 && (!range_pinned(A, is_t(transA) ? K : s->M, is_t(transA) ? s->M : K, lda, 8) ||
+                  !range_pinned(B, is_t(transB) ? s->N : K, is_t(transB) ? K : s->N, ldb, 8)))
+        return fail(OOC_ERR_NOT_PINNED, "host operands must be page-locked (cudaHostAlloc / cudaHostRegister)");
+    PlanRequest rq = session_request(*s, transA, transB, K, s->nR, s->calls);
+    rq.lda = lda;
+    rq.ldb = ldb;
+    Exec x;
+    x.flags = s->opts.flags;
+    if ((rc = make_plan(rq, x.p, why))) return fail(rc, why);
+    const Plan& p = x.p;
+    if (p.mb != s->mb || p.nb != s->nb || p.nR != s->nR || p.device_bytes > s->budget)
+        return fail(OOC_ERR_BUDGET, "this call's operand rings do not fit beside the resident C blocks");
+    std::vector<Op> ops;
+    build_schedule(p, ops);
+    x.arena = s->arena;
+    x.own_arena = false;
+    x.own_streams = false;
+    for (int i = 0; i < 3; ++i) x.st[i] = s->st[i];
+    Inject inj;
+    Operands o{A, lda, B, ldb, s->C, s->ldc, alpha, s->beta};
+    ooc_stats st;
+    std::memset(&st, 0, sizeof(st));
+    if ((rc = execute(x, ops, o, 8, inj, &st))) return rc;
+    x.release();
+    s->c_slot = p.c_slot + p.c_aux;
+    s->header = p.header;
+    s->ldc_dev = p.ldc_dev;
+    s->h2d += st.h2d_bytes;
+    s->d2h += st.d2h_bytes;
+    s->kernel_s += st.kernel_seconds;
+    s->device_s += st.device_seconds;
+    s->launches += st.kernel_launches;
+    s->steps += st.steps;
+    s->flops += 2.0 * (double)s->M * s->N * K;
+    ++s->calls;
+    if (stats) {
+        *stats = st;
+        stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_host0).count();
+        stats->tflops = stats->seconds > 0 ? 2.0 * (double)s->M * s->N * K / stats->seconds / 1e12 : 0.0;
+    }
+    return OOC_OK;
+}
+
+int ooc_session_query(const ooc_session* s, int64_t* mb, int64_t* nb, int64_t* resident_blocks, int64_t* blocks,
+                      int32_t* calls)
+{
+    if (!s) return fail(OOC_ERR_INVALID_ARG, "null session");
+    if (mb) *mb = s->mb;
+    if (nb) *nb = s->nb;
+    if (resident_blocks) *resident_blocks = s->nR;
+    if (blocks) *blocks = s->h * s->w;
+    if (calls) *calls = s->calls;
+    return OOC_OK;
+}
+
+int ooc_session_finish(ooc_session* s, ooc_stats* stats)
+{
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    if (!s) return fail(OOC_ERR_INVALID_ARG, "null session");
+    std::unique_ptr<ooc_session> own(s);
+    int rc;
+    if (s->calls == 0) {
+        // no product was added: C = beta * C
+        if ((rc = ooc_session_step(s, 'N', 'N', 0, 0.0, nullptr, 1, nullptr, 1, nullptr))) return rc;
+    }
+    // the resident blocks go back to the host (schedule order: block column j outer, row i inner)
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaEventRecord(e0, s->st[kStreamD2H]));
+    for (int64_t r = 0; r < s->nR; ++r) {
+        const int64_t j = r / s->h, i = r % s->h;
+        const int64_t rows = std::min(s->mb, s->M - i * s->mb), cols = std::min(s->nb, s->N - j * s->nb);
+        const char* src = s->arena + s->header + (size_t)r * s->c_slot;
+        double* dst = s->C + i * s->mb * s->ldc + j * s->nb;
+        CK(cudaMemcpy2DAsync(dst, s->ldc * 8, src, s->ldc_dev * 8, cols * 8, rows, cudaMemcpyDeviceToHost,
+                             s->st[kStreamD2H]));
+        s->d2h += (double)rows * cols * 8;
+    }
+    CK(cudaEventRecord(e1, s->st[kStreamD2H]));
+    CK(cudaStreamSynchronize(s->st[kStreamD2H]));
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    s->device_s += ms * 1e-3;
+    if (stats) {
+        stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - s->t0).count();
+        stats->device_seconds = s->device_s;
+        stats->kernel_seconds = s->kernel_s;
+        stats->tflops = stats->seconds > 0 ? s->flops / stats->seconds / 1e12 : 0.0;
+        stats->h2d_bytes = s->h2d;
+        stats->d2h_bytes = s->d2h;
+        stats->mb = s->mb; stats->nb = s->nb;
+        stats->form = s->opts.form;
+        stats->blocks = s->h * s->w;
+        stats->steps = s->steps;
+        stats->device_bytes = (int64_t)s->budget;
+        stats->kernel_launches = s->launches;
+    }
+    return OOC_OK;
+}
+
+int ooc_session_free(ooc_session* s)
+{
+    delete s;
+    return OOC_OK;
+}
+
+int ooc_schedule_session(int64_t M, int64_t N, int64_t K, int32_t beta_nonzero, size_t budget, const ooc_opts* opts_in,
+                         int32_t resident_blocks, int32_t call, ooc_stats* plan, ooc_sched_op* out, int64_t capacity,
+                         int64_t* count)
+{
+    if (M <= 0 || N <= 0 || K < 0 || !count || resident_blocks < 0 || call < 0)
+        return fail(OOC_ERR_INVALID_ARG, "ooc_schedule_session: bad arguments");
+    ooc_opts opts;
+    std::memset(&opts, 0, sizeof(opts));
+    if (opts_in) opts = *opts_in;
+    PlanRequest rq{M, N, K, 8, beta_nonzero != 0, false, false, budget, opts};
+    rq.nR = resident_blocks;
+    rq.session_step = call;
+    return export_schedule(rq, plan, out, capacity, count);
+}

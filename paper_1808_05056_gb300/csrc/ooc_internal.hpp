@@ -40,11 +40,19 @@ struct Plan {
     // (tri 1, lower) or col - row >= tri_off (tri 2, upper) of C are updated.
     int32_t tri = 0;
     int64_t tri_off = 0;
+    // Session mode (Section IV's nsteps invocations): the first nR updated
+    // blocks in schedule order keep a dedicated device slot for the whole
+    // session (slots nA + nB + nC ..), placed first in the arena so that every
+    // call of the session finds them at the same address.  session_step is -1
+    // for a single call, 0 for a session's first call, > 0 for later calls
+    // (which accumulate onto the partial sums instead of applying beta).
+    int32_t nR = 0;
+    int32_t session_step = -1;
 
     int64_t rows_of(int64_t i) const { return (i + 1) * mb <= M ? mb : M - i * mb; }
     int64_t cols_of(int64_t j) const { return (j + 1) * nb <= N ? nb : N - j * nb; }
     int64_t k_of(int64_t c) const { return (c + 1) * kb <= K ? kb : K - c * kb; }
-    int32_t slots() const { return nA + nB + nC; }
+    int32_t slots() const { return nA + nB + nC + nR; }
     // 0: block (i, j) holds no updated element (skipped); 1: all of it is
     // updated; 2: it straddles the edge of the updated part (masked epilogue,
     // and the block is loaded so that its other elements go back unchanged)
@@ -70,6 +78,8 @@ struct PlanRequest {
     int64_t lda = 0, ldb = 0, ldc = 0;          // host leading dimensions (0: rows are contiguous)
     int32_t tri = 0;                            // triangular update of C (Plan::tri)
     int64_t tri_off = 0;
+    int32_t nR = 0;                             // resident C blocks (Plan::nR)
+    int32_t session_step = -1;
 };
 
 // Returns OOC_OK and fills `plan`, or an error code with a message in `why`.

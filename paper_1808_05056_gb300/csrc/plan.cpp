@@ -105,8 +105,8 @@ void layout(Plan& p, const FormModel& f)
         p.b_aux = split_aux_bytes(p, p.nb);
     }
     (void)f;
-    p.device_bytes = p.header + (size_t)p.nA * (p.a_slot + p.a_aux) +
-                     (size_t)p.nB * (p.b_slot + p.b_aux) + (size_t)p.nC * (p.c_slot + p.c_aux);
+    p.device_bytes = p.header + (size_t)p.nA * (p.a_slot + p.a_aux) + (size_t)p.nB * (p.b_slot + p.b_aux) +
+                     (size_t)(p.nC + p.nR) * (p.c_slot + p.c_aux);
 }
 
 // The updated blocks of block column j: block rows [lo, hi) are updated, of
@@ -169,8 +169,11 @@ void traffic(Plan& p)
         double a_loads = (p.h == 1 && p.nkc <= p.nA) ? A : A * p.w;
         double b_loads = (p.nkc <= p.nB) ? B : B * p.h;
         if (p.K == 0) a_loads = b_loads = 0;
-        p.h2d_bytes = a_loads + b_loads + (p.beta_nz ? C : 0.0);
-        p.d2h_bytes = C;
+        // resident blocks of a session move only on the first call (beta != 0) and at its end
+        const double streamed = 1.0 - (double)p.nR / (double)std::max<int64_t>(1, p.h * p.w);
+        const bool later = p.session_step > 0;
+        p.h2d_bytes = a_loads + b_loads + (later ? C * streamed : (p.beta_nz ? C : 0.0));
+        p.d2h_bytes = C * streamed;
         return;
     }
     double a_loads = 0, b_loads = 0, c_in = 0, c_out = 0;
@@ -304,6 +307,7 @@ int make_plan(const PlanRequest& rq, Plan& p, std::string& why)
     p.M = rq.M; p.N = rq.N; p.K = rq.K; p.es = rq.es;
     p.beta_nz = rq.beta_nz; p.ta = rq.ta; p.tb = rq.tb;
     p.tri = rq.tri; p.tri_off = rq.tri_off;
+    p.nR = rq.nR; p.session_step = rq.session_step;
     p.lda_host = rq.lda; p.ldb_host = rq.ldb; p.ldc_host = rq.ldc;
     int form = rq.opts.form;
     if (form == OOC_FORM_AUTO) form = (rq.es == 8) ? OOC_FORM_FP64 : OOC_FORM_BF16X3;
@@ -387,6 +391,8 @@ int make_plan(const PlanRequest& rq, Plan& p, std::string& why)
                             c.mb = mb; c.nb = nb; c.kb = kb;
                             c.h = cdiv(rq.M, mb); c.w = cdiv(rq.N, nb); c.nkc = nkc;
                             c.nA = nA; c.nB = nB; c.nC = nC;
+                            if (c.nR > c.h * c.w) continue;        // resident blocks need this blocking
+                            if (c.nR == c.h * c.w) c.nC = 0;       // every block resident: no C ring
                             layout(c, f);
                             if (c.device_bytes > rq.budget) continue;
                             traffic(c);
@@ -471,7 +477,9 @@ void plan_features(const Plan& p, const PlanRequest& rq, float* f)
 
 size_t slot_offset(const Plan& p, int32_t s)
 {
-    size_t off = p.header;
+    const int32_t ring = p.nA + p.nB + p.nC;
+    if (s >= ring) return p.header + (size_t)(s - ring) * (p.c_slot + p.c_aux);  // resident C slots come first
+    size_t off = p.header + (size_t)p.nR * (p.c_slot + p.c_aux);
     if (s < p.nA) return off + (size_t)s * (p.a_slot + p.a_aux);
     off += (size_t)p.nA * (p.a_slot + p.a_aux);
     s -= p.nA;
@@ -576,9 +584,15 @@ struct Gen {
             for (int64_t i = 0; i < p.h; ++i) {
                 const int cls = p.block_class(i, j);
                 if (cls == 0) continue;  // no element of this block is updated
-                // a block straddling a triangular update's edge goes back whole, so it is loaded even for beta == 0
-                const bool load_c = p.beta_nz || cls == 2;
-                const int sc = c0 + (int)(nblk++ % p.nC);
+                // session: the first nR blocks keep their own slot across the session's calls
+                const bool resident = nblk < p.nR;
+                const int sc = resident ? c0 + p.nC + (int)nblk : c0 + (int)((nblk - p.nR) % p.nC);
+                ++nblk;
+                // a later session call adds onto partial sums: a resident block's are in its slot,
+                // a streamed block's come back from the host.  A block straddling a triangular
+                // update's edge goes back whole, so it is loaded even for beta == 0.
+                const bool later = p.session_step > 0;
+                const bool load_c = later ? !resident : (p.beta_nz || cls == 2);
                 for (int64_t kc = 0; kc < p.nkc; ++kc) {
                     const int64_t t = step_index(i, j, kc);
                     int sa = -1, sb = -1;
@@ -614,10 +628,10 @@ struct Gen {
                     }
                     Op k; k.kind = kKernel; k.stream = kStreamCompute;
                     k.i = i; k.j = j; k.kc = kc;
-                    k.first = (kc == 0); k.last = (kc == p.nkc - 1);
+                    k.first = (kc == 0) && !later; k.last = (kc == p.nkc - 1);
                     if (sa >= 0) { k.rslot[k.nr] = sa; k.rtag[k.nr] = content[sa]; ++k.nr; }
                     if (sb >= 0) { k.rslot[k.nr] = sb; k.rtag[k.nr] = content[sb]; ++k.nr; }
-                    if (kc > 0 || load_c) { k.rslot[k.nr] = sc; k.rtag[k.nr] = content[sc]; ++k.nr; }
+                    if (kc > 0 || load_c || later) { k.rslot[k.nr] = sc; k.rtag[k.nr] = content[sc]; ++k.nr; }
                     k.wslot = sc;
                     k.wtag = Tag{kMatC, i, j, kc + 1};
                     push(k);
@@ -627,7 +641,7 @@ struct Gen {
                         read_since_load[s] = true;
                         emit_record(kStreamCompute, ev_free(p, s));
                     }
-                    if (kc == p.nkc - 1) {
+                    if (kc == p.nkc - 1 && !resident) {
                         emit_record(kStreamCompute, ev_done(p, sc));
                         emit_wait(kStreamD2H, ev_done(p, sc));
                         Op d; d.kind = kD2H; d.stream = kStreamD2H; d.nr = 1;

@@ -261,3 +261,51 @@ def test_triangular_plan_moves_about_half_the_bytes():
     assert tri["blocks"] == 8 * 9 // 2 and full["blocks"] == 64
     assert tri["d2h_bytes"] == pytest.approx(full["d2h_bytes"] * 36 / 64)
     assert tri["seconds"] < 0.7 * full["seconds"]
+
+
+# ---- sessions (Section IV nsteps: one C over several calls) ----------------------
+SESSION_CASES = [
+    # (M, N, K, beta, mb, nb, resident blocks, call)
+    (300, 200, 170, 1, 64, 64, 0, 0),
+    (300, 200, 170, 1, 64, 64, 5, 0),
+    (300, 200, 170, 0, 64, 64, 5, 1),
+    (300, 200, 170, 1, 64, 64, 20, 2),     # every block resident: no C ring, no C copies
+    (300, 200, 170, 0, 128, 64, 3, 0),
+    (1000, 700, 300, 1, 256, 128, 7, 3),
+]
+
+
+@pytest.mark.parametrize("case", range(len(SESSION_CASES)))
+def test_session_call_schedule(case):
+    M, N, K, beta, mb, nb, nres, call = SESSION_CASES[case]
+    opts = P.make_opts(mb=mb, nb=nb, kb=64, depth=2)
+    plan, ops = P.ooc_schedule_session(M, N, K, beta, 1 << 40, opts, nres, call)
+    h, w = -(-M // mb), -(-N // nb)
+    order = [(i, j) for j in range(w) for i in range(h)]       # schedule order of the blocks
+    resident = set(order[:nres])
+    ring = plan["depth"] + plan["b_buffers"] + plan["c_buffers"]
+    res_slot = {b: ring + r for r, b in enumerate(order[:nres])}
+    initial = [(res_slot[b], (2, b[0], b[1], 0)) for b in resident] if call > 0 else []
+    chk = to_checker(ops)
+    assert pipeline.check(chk, initial=initial) == []
+    if call > 0 and resident:
+        assert pipeline.check(chk)          # without the carried-over contents the reads are unfed
+    # resident blocks never leave the device; every other block goes back exactly once
+    nkc = plan["steps"] // (h * w)
+    finals = sorted(t for _, t in pipeline.final_host_writes(chk))
+    assert finals == sorted((2, i, j, nkc) for i, j in order if (i, j) not in resident)
+    loads = {(o["write_tag"][1], o["write_tag"][2]) for o in ops if o["kind"] == 0 and o["write_tag"][0] == 2}
+    if call == 0:
+        assert loads == (set(order) if beta else set())
+    else:
+        assert loads == set(order) - resident           # partial sums come back from the host
+    # resident blocks live in their own slots; the kernels of a later call accumulate
+    for o in ops:
+        if o["kind"] == 1:
+            _, i, j, v = o["write_tag"]
+            if (i, j) in resident:
+                assert o["write_slot"] == res_slot[(i, j)]
+            if call > 0:
+                assert (2, i, j, v - 1) in o["read_tag"]
+    if nres == h * w:
+        assert plan["c_buffers"] == 0
