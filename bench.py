@@ -47,13 +47,15 @@ CONFIGS = {
     "syrk-32768": ("syrk", 32768, 32768, 16384, 1.0, 0.5, 4 << 30, synth.NORMAL),
     "trsm-32768": ("trsm", 32768, 32768, 0, 1.0, 0.0, 4 << 30, synth.UNIFORM),
     "potrf-32768": ("potrf", 32768, 32768, 0, 1.0, 0.0, 4 << 30, synth.NORMAL),
+    # Section IV nsteps: 4 SUMMA-style calls of K = 4096 each into one 65536^2 C, Ozaki form, C resident in HBM
+    "summa-65536": ("summa", 65536, 65536, 16384, 1.0, 0.5, 48 << 30, synth.NORMAL),
 }
 LEVEL3 = ("syrk", "trsm", "potrf")
 # per form: (element dtype name, relative Frobenius tolerance, products per logical product, dtype tag)
 FORMS = {"fp64": ("float64", 1e-13, 1, "f64"), "ozaki": ("float64", 1e-12, 36, "f64 (bf16 digit planes)"),
          "bf16x3": ("float32", 1e-6, 6, "f32 (bf16x3 pieces)"), "batched": ("float64", 1e-13, 1, "f64"),
          "syrk": ("float64", 1e-13, 1, "f64"), "trsm": ("float64", 1e-12, 1, "f64"),
-         "potrf": ("float64", 1e-12, 1, "f64")}
+         "potrf": ("float64", 1e-12, 1, "f64"), "summa": ("float64", 1e-12, 36, "f64 (bf16 digit planes)")}
 
 
 def batch_shapes(seed, count, lo, hi, cap=64 << 30, es=8):
@@ -788,6 +790,154 @@ def run_level3_bench(args, w, world, rank, local, pg):
     print(json.dumps(line), flush=True)
 
 
+def run_summa_bench(args, w, world, rank, local, pg):
+    """nsteps configuration: one session (create, 4 calls, finish) per step, against the same
+    calls made one by one with ooc_dgemm (every C block crosses the link in every call)."""
+    import torch
+    M, N, K = w["M"], w["N"], w["K"]
+    nsteps = 4
+    ks = K // nsteps
+    cores = host_cores()
+    panels = []
+    for q in range(nsteps):
+        A = torch.empty((M, ks), dtype=torch.float64, pin_memory=True)
+        B = torch.empty((ks, N), dtype=torch.float64, pin_memory=True)
+        synth.fill(A, 500 + q + 1000 * rank, 0, w["dist"])
+        synth.fill(B, 500 + q + 1000 * rank, 1, w["dist"])
+        panels.append((A, B, 1.0 if q % 2 == 0 else -0.5))
+    C = torch.empty((M, N), dtype=torch.float64, pin_memory=True)
+    C0 = torch.empty_like(C, pin_memory=True)
+    synth.fill(C0, 500 + 1000 * rank, 2, w["dist"])
+    flops = 2.0 * M * N * K
+    desc = ("out-of-core C = beta C + sum of %d calls alpha_s A_s B_s (SUMMA-style steps), M=N=%d, K=%d per call, "
+            "Ozaki form, beta=%g, N(0,1), device budget %.0f GiB" % (nsteps, M, ks, w["beta"], w["budget"] / 2 ** 30))
+    cfg = {"workload": desc, "form": "summa", "M": M, "N": N, "K_per_call": ks, "calls": nsteps,
+           "device_budget_bytes": w["budget"], "l2": "inputs larger than L2: 48 GiB of host operands per step"}
+    r = 64
+    blocks = sample_blocks(w, 8, r)
+
+    def oracle_blocks():
+        import oracle
+        out, t0 = [], time.perf_counter()
+        for i, j in blocks:
+            cur = C0[i:i + r, j:j + r].numpy().astype(np.float64)
+            for q, (A, B, alpha) in enumerate(panels):
+                b = w["beta"] if q == 0 else 1.0
+                cur, _ = oracle.gemm_block("N", "N", i, j, r, r, ks, alpha, A.numpy(), B.numpy(), b, cur,
+                                           nthreads=cores)
+            out.append(cur)
+        return out, time.perf_counter() - t0
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        times = []
+        for it in range(args.warmup + args.steps):
+            _, dt = oracle_blocks()
+            if it >= args.warmup:
+                times.append(dt)
+        value = 2.0 * r * r * K * len(blocks) * len(times) / sum(times) / 1e12
+        line = {"impl": "reference", "metric": "out-of-core nsteps GEMM effective TFLOP/s incl. transfers",
+                "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Philox)", "config": cfg,
+                "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                                 "sample": "%d seeded %dx%d blocks of C through all %d calls" % (
+                                     len(blocks), r, r, nsteps)},
+                "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+    import paper_1808_05056_gb300 as P
+    torch.cuda.set_device(local)
+    P.load()
+    opts = P.make_opts(form=P.OOC_FORM_OZAKI)
+
+    def session_step():
+        C.copy_(C0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s = P.Session(M, N, C, N, w["beta"], w["budget"], k_hint=ks, opts=opts)
+        if s.rc != 0:
+            raise RuntimeError("session: %s" % P.ooc_last_error())
+        info = s.query()
+        for A, B, alpha in panels:
+            if s.step("N", "N", ks, alpha, A, ks, B, N) != 0:
+                raise RuntimeError("session step: %s" % P.ooc_last_error())
+        st = P.ooc_stats()
+        if s.finish(st) != 0:
+            raise RuntimeError("session finish: %s" % P.ooc_last_error())
+        return time.perf_counter() - t0, st, info
+
+    def plain_step():
+        C.copy_(C0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h2d = d2h = 0.0
+        for q, (A, B, alpha) in enumerate(panels):
+            st = P.ooc_stats()
+            rc = P.ooc_dgemm("N", "N", M, N, ks, alpha, A, ks, B, N, w["beta"] if q == 0 else 1.0, C, N,
+                             w["budget"], opts, st)
+            if rc != 0:
+                raise RuntimeError("ooc_dgemm: %s" % P.ooc_last_error())
+            h2d += st.h2d_bytes
+            d2h += st.d2h_bytes
+        return time.perf_counter() - t0, h2d, d2h
+
+    for _ in range(max(0, args.warmup - 1)):
+        session_step()
+    session_step()
+    parity = cpu = None
+    if rank == 0:
+        ref, dt = oracle_blocks()
+        errs = [float(np.linalg.norm(C[i:i + r, j:j + r].numpy() - rv) / np.linalg.norm(rv))
+                for (i, j), rv in zip(blocks, ref)]
+        parity = {"max_rel_fro": max(errs), "tolerance": FORMS["summa"][1], "blocks": len(blocks), "block": r,
+                  "pass": max(errs) <= FORMS["summa"][1]}
+        cpu = {"value": 2.0 * r * r * K * len(blocks) / dt / 1e12, "unit": "TFLOP/s", "cores": cores,
+               "kind": "oracle", "sample": "%d seeded %dx%d blocks of C through all %d calls, %.1f s" % (
+                   len(blocks), r, r, nsteps, dt)}
+    clk = ClockSampler(local, enabled=not args.no_clocks)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    runs = [session_step() for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    clocks = clk.stop()
+    wall = sum(x[0] for x in runs)
+    if pg:
+        import torch.distributed as dist
+        t = torch.tensor([wall], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        wall = t.item()
+    plain_t, plain_h2d, plain_d2h = plain_step()   # comparison, outside the timed region
+    if rank != 0:
+        return
+    _, st, info = runs[0]
+    pk, pk_src = peaks()
+    value = world * flops * args.steps / wall / 1e12
+    peak = pk["bf16_tflops_sustained"]
+    line = {
+        "metric": "out-of-core nsteps GEMM effective TFLOP/s incl. transfers", "value": value, "unit": "TFLOP/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": FORMS["summa"][3],
+        "data": "synthetic (seeded Philox, pinned host)", "config": cfg,
+        "roofline": {"bound": "tensor", "kernel": "tc_terms_kernel (Ozaki, tcgen05)",
+                     "achieved": flops * 36 / st.kernel_seconds / 1e12, "peak": peak, "unit": "TFLOP/s",
+                     "frac": flops * 36 / st.kernel_seconds / 1e12 / peak, "traffic": None,
+                     "peak_source": "%s bf16 sustained (cuBLAS) %.1f TF" % (pk_src, peak)},
+        "session": {"resident_blocks": info["resident_blocks"], "blocks": info["blocks"], "mb": info["mb"],
+                    "nb": info["nb"], "h2d_bytes": st.h2d_bytes, "d2h_bytes": st.d2h_bytes},
+        "without_session": {"value": flops / plain_t / 1e12, "unit": "TFLOP/s", "h2d_bytes": plain_h2d,
+                            "d2h_bytes": plain_d2h, "note": "the same %d calls as plain ooc_dgemm" % nsteps},
+        "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": st.h2d_bytes,
+                "d2h_bytes_per_step": st.d2h_bytes},
+        "gpu_launches": st.kernel_launches, "parity": parity, "cpu_baseline": cpu, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     w = workload(args)
@@ -795,6 +945,8 @@ def main():
     args.gpus = world if world > 1 else args.gpus
     if w["form"] in LEVEL3:
         run_level3_bench(args, w, world, rank, local, pg)
+    elif w["form"] == "summa":
+        run_summa_bench(args, w, world, rank, local, pg)
     elif w["form"] == "batched":
         run_batched_bench(args, w, world, rank, local, pg)
     elif args.impl == "reference":

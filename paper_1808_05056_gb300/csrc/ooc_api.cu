@@ -1405,7 +1405,7 @@ int ooc_session_finish(ooc_session* s, ooc_stats* stats)
     int rc;
     if (s->calls == 0) {
         // no product was added: C = beta * C
-        if ((rc = ooc_session_step(s, 'N', 'N', 0, 0.0, nullptr, 1, nullptr, 1, nullptr))) return rc;
+        if ((rc = ooc_session_step(s, 'N', 'N', 0, 0.0, nullptr, 1, nullptr, s->N, nullptr))) return rc;
     }
     // the resident blocks go back to the host (schedule order: block column j outer, row i inner)
     cudaEvent_t e0 = nullptr, e1 = nullptr;
