@@ -47,7 +47,7 @@ CONFIGS = {
     "syrk-32768": ("syrk", 32768, 32768, 16384, 1.0, 0.5, 4 << 30, synth.NORMAL),
     "trsm-32768": ("trsm", 32768, 32768, 0, 1.0, 0.0, 4 << 30, synth.UNIFORM),
     "potrf-32768": ("potrf", 32768, 32768, 0, 1.0, 0.0, 4 << 30, synth.NORMAL),
-    # Section IV nsteps: 4 SUMMA-style calls of K = 4096 each into one 65536^2 C, Ozaki form, C resident in HBM
+    # Section IV nsteps: 4 SUMMA-style calls with 4096-wide panels into one 65536^2 C, Ozaki form, C resident in HBM
     "summa-65536": ("summa", 65536, 65536, 16384, 1.0, 0.5, 48 << 30, synth.NORMAL),
 }
 LEVEL3 = ("syrk", "trsm", "potrf")
@@ -795,8 +795,9 @@ def run_summa_bench(args, w, world, rank, local, pg):
     calls made one by one with ooc_dgemm (every C block crosses the link in every call)."""
     import torch
     M, N, K = w["M"], w["N"], w["K"]
-    nsteps = 4
-    ks = K // nsteps
+    ks = 4096                      # SUMMA panel width
+    nsteps = max(1, K // ks)
+    K = ks * nsteps
     cores = host_cores()
     panels = []
     for q in range(nsteps):
@@ -812,7 +813,8 @@ def run_summa_bench(args, w, world, rank, local, pg):
     desc = ("out-of-core C = beta C + sum of %d calls alpha_s A_s B_s (SUMMA-style steps), M=N=%d, K=%d per call, "
             "Ozaki form, beta=%g, N(0,1), device budget %.0f GiB" % (nsteps, M, ks, w["beta"], w["budget"] / 2 ** 30))
     cfg = {"workload": desc, "form": "summa", "M": M, "N": N, "K_per_call": ks, "calls": nsteps,
-           "device_budget_bytes": w["budget"], "l2": "inputs larger than L2: 48 GiB of host operands per step"}
+           "device_budget_bytes": w["budget"],
+           "l2": "inputs larger than L2: %.0f GiB of host operands per step" % ((M * N + K * (M + N)) * 8 / 2 ** 30)}
     r = 64
     blocks = sample_blocks(w, 8, r)
 
