@@ -361,6 +361,52 @@ int ooc_schedule_session(int64_t M, int64_t N, int64_t K, int32_t beta_nonzero,
                          int32_t call, ooc_stats* plan, ooc_sched_op* out, int64_t capacity,
                          int64_t* count);
 
+/* ---- pipeline-description language (end of Section IV) ------------------ */
+/*
+ * Section IV closes by noting that the event synchronisation of its pipeline
+ * is a pattern shared by out-of-core data-parallel kernels, and proposes a
+ * pattern language from which a compiler writes that code.  A description
+ * (text, one statement per line, '#' starts a comment):
+ *
+ *   operand NAME tile ROWS COLS ring SLOTS    host matrix cut into tiles; SLOTS device slots
+ *   for VAR in LO .. HI   ...   end           loop (HI exclusive)
+ *   load  NAME[ROW, COL]  [if VAR | unless VAR]   tile to the device (no copy when resident)
+ *   alloc NAME[ROW, COL]  [if VAR | unless VAR]   slot for a tile written without being read
+ *   run   KERNEL OUT[..] IN[..] ...               OUT is written, the rest are read
+ *   store NAME[ROW, COL]  [if VAR | unless VAR]   tile back to the host
+ *
+ * Integer expressions: + - * / ( ), numbers, variables (ooc_pipe_set), loop
+ * variables, trows(NAME) / tcols(NAME) = tile rows / columns of an operand.
+ * Kernels (FP64 operands): gemm C A B -- C = alpha A B + beta C when C was
+ * loaded, alpha A B when allocated, C + alpha A B when already written by an
+ * earlier run; axpby Y X -- Y = a X + b Y (a X when Y was allocated); alpha,
+ * beta, a, b are variables (defaults 1, 0, 1, 1).
+ *
+ * The compiler runs the loop nest on the host and emits copies and kernels
+ * on an H2D, a compute and a D2H stream with exactly the events the Section IV
+ * hazard rule requires (slots reused least recently used first).  A tile
+ * written and never stored, a kernel on a tile that is not resident, tile
+ * shapes a kernel cannot take, or an unknown name are errors
+ * (OOC_ERR_INVALID_ARG; ooc_last_error() names the line).
+ *
+ * ooc_pipe_create parses; ooc_pipe_set sets a variable; ooc_pipe_bind gives
+ * an operand its host matrix (row-major rows x cols, leading dimension ld,
+ * elem_bytes 8 for the kernels; host may be NULL for ooc_pipe_schedule);
+ * ooc_pipe_schedule compiles and exports the schedule (as ooc_schedule;
+ * plan: device_bytes, bytes moved, steps = kernels, blocks = stores);
+ * ooc_pipe_run compiles and executes synchronously in one arena of at most
+ * device_budget_bytes (pinned host operands); ooc_pipe_free releases.
+ */
+typedef struct ooc_pipe ooc_pipe;
+int ooc_pipe_create(const char* description, ooc_pipe** pipe);
+int ooc_pipe_set(ooc_pipe* pipe, const char* name, double value);
+int ooc_pipe_bind(ooc_pipe* pipe, const char* operand, void* host, int64_t rows, int64_t cols,
+                  int64_t ld, int32_t elem_bytes);
+int ooc_pipe_schedule(ooc_pipe* pipe, size_t device_budget_bytes, ooc_stats* plan, ooc_sched_op* out,
+                      int64_t capacity, int64_t* count);
+int ooc_pipe_run(ooc_pipe* pipe, size_t device_budget_bytes, ooc_stats* stats);
+int ooc_pipe_free(ooc_pipe* pipe);
+
 /* ---- plan search: candidates, autotuner, learned cost model ------------ */
 /* The paper has no plan search beyond its partitioner (Section IV); these
  * calls pick block/chunk/ring sizes for this hardware. */

@@ -134,6 +134,12 @@ def load(path=None):
     lib.ooc_session_query.argtypes = [sp] + [ctypes.POINTER(i64)] * 4 + [ctypes.POINTER(i32)]
     lib.ooc_schedule_session.argtypes = [i64, i64, i64, i32, sz, po, i32, i32, ps, ctypes.POINTER(ooc_sched_op),
                                          i64, ctypes.POINTER(i64)]
+    lib.ooc_pipe_create.argtypes = [ctypes.c_char_p, ctypes.POINTER(sp)]
+    lib.ooc_pipe_set.argtypes = [sp, ctypes.c_char_p, dbl]
+    lib.ooc_pipe_bind.argtypes = [sp, ctypes.c_char_p, vp, i64, i64, i64, i32]
+    lib.ooc_pipe_schedule.argtypes = [sp, sz, ps, ctypes.POINTER(ooc_sched_op), i64, ctypes.POINTER(i64)]
+    lib.ooc_pipe_run.argtypes = [sp, sz, ps]
+    lib.ooc_pipe_free.argtypes = [sp]
     lib.ooc_query_device.argtypes = [ctypes.POINTER(sz), ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
     lib.ooc_strerror.argtypes = [ctypes.c_int]
     lib.ooc_strerror.restype = ctypes.c_char_p
@@ -142,7 +148,8 @@ def load(path=None):
     for f in ("ooc_dgemm", "ooc_sgemm", "ooc_dgemm_device", "ooc_plan", "ooc_schedule", "ooc_query_device",
               "ooc_dgemmt", "ooc_dsyrk", "ooc_ssyrk", "ooc_schedule_gemmt", "ooc_dtrsm", "ooc_dpotrf",
               "ooc_session_create", "ooc_session_step", "ooc_session_finish", "ooc_session_free",
-              "ooc_session_query", "ooc_schedule_session"):
+              "ooc_session_query", "ooc_schedule_session", "ooc_pipe_create", "ooc_pipe_set", "ooc_pipe_bind",
+              "ooc_pipe_schedule", "ooc_pipe_run", "ooc_pipe_free"):
         getattr(lib, f).restype = ctypes.c_int
     if path is None:
         _lib = lib
@@ -264,6 +271,67 @@ class Session:
         if self._h:
             load().ooc_session_free(self._h)
             self._h = ctypes.c_void_p()
+
+
+class Pipe:
+    """A pipeline description compiled by the library (ooc_pipe_*)."""
+
+    def __init__(self, description):
+        self._h = ctypes.c_void_p()
+        self.rc = load().ooc_pipe_create(description.encode(), ctypes.byref(self._h))
+
+    def set(self, name, value):
+        return load().ooc_pipe_set(self._h, name.encode(), float(value))
+
+    def bind(self, operand, host=None, rows=None, cols=None, ld=None, elem_bytes=8):
+        """Bind an operand to a pinned host tensor / array (or to dimensions only, for schedule())."""
+        if host is not None and rows is None:
+            rows, cols = host.shape
+            ld = _ld(host)
+            elem_bytes = host.element_size() if hasattr(host, "element_size") else host.itemsize
+        return load().ooc_pipe_bind(self._h, operand.encode(), _ptr(host), rows, cols, ld or cols, elem_bytes)
+
+    def schedule(self, budget):
+        lib = load()
+        st = ooc_stats()
+        ops = _export(lambda buf, cap, n: lib.ooc_pipe_schedule(self._h, budget, ctypes.byref(st), buf, cap, n),
+                      "ooc_pipe_schedule")
+        return st.as_dict(), ops
+
+    def run(self, budget, stats=None):
+        return load().ooc_pipe_run(self._h, budget, _ref(stats))
+
+    def free(self):
+        if self._h:
+            load().ooc_pipe_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+# The out-of-core GEMM of Section IV written in the pipeline language: block
+# column j outer, block row i inner, K chunks innermost; C loaded only for beta != 0.
+MMOOC_PIPELINE = """
+operand A tile mb kb ring ra
+operand B tile kb nb ring rb
+operand C tile mb nb ring rc
+for j in 0 .. tcols(C)
+  for i in 0 .. trows(C)
+    load C[i, j] if beta_nz
+    alloc C[i, j] unless beta_nz
+    for k in 0 .. tcols(A)
+      load A[i, k]
+      load B[k, j]
+      run gemm C[i, j] A[i, k] B[k, j]
+    end
+    store C[i, j]
+  end
+end
+"""
 
 
 def ooc_schedule_session(M, N, K, beta_nonzero, budget, opts, resident_blocks, call):

@@ -1,8 +1,11 @@
 // Internal interfaces of libooc: the plan, the issued schedule and the kernel
 // launchers.  Host-only declarations; nothing here is exported.
 #pragma once
+#include <algorithm>
 #include <cstddef>
 #include <cstdint>
+#include <map>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -122,6 +125,8 @@ struct Op {
     // execution detail
     int64_t i = 0, j = 0, kc = 0;  // block row, block column, K chunk
     bool first = false, last = false;
+    int32_t kernel = -1;           // pipeline-language kernels: which built-in
+    int32_t mode = 0;              // and how its output tile starts (pipe.cpp)
 };
 
 // Events: ready(s) after a load into slot s, free(s) after a kernel read s,
@@ -144,6 +149,44 @@ size_t split_aux_bytes(const Plan& p, int64_t rows);
 // slot byte offsets inside the arena
 size_t slot_offset(const Plan& p, int32_t slot);
 size_t slot_aux_offset(const Plan& p, int32_t slot);
+
+// ------------------------------------------------- pipeline language --
+// A compiled pipeline description (pipe.cpp): the operands' tiles and rings,
+// and the schedule with its events, ready for the executor (pipe_exec.cu).
+struct PipeOperand {
+    std::string name;
+    void* host = nullptr;
+    int64_t rows = 0, cols = 0, ld = 0;
+    int32_t es = 8;
+    int64_t tr = 0, tc = 0;      // tile rows / columns
+    int32_t ring = 0;            // device slots
+    int32_t slot0 = 0;           // its first slot (global slot numbering)
+    int64_t ld_dev = 0;          // slot leading dimension (elements)
+    size_t slot_bytes = 0;
+    bool bound = false;
+    int64_t tile_rows(int64_t r) const { return std::min(tr, rows - r * tr); }
+    int64_t tile_cols(int64_t c) const { return std::min(tc, cols - c * tc); }
+};
+
+struct PipeProgram {
+    std::vector<PipeOperand> operands;
+    std::vector<Op> ops;
+    int32_t slots = 0, events = 0;
+    size_t header = 256, device_bytes = 0;
+    std::vector<size_t> slot_off;            // byte offset of each slot in the arena
+};
+
+enum PipeKernel { kPipeGemm = 0, kPipeAxpby = 1 };
+// how the output tile of a kernel op starts: loaded from the host (apply the
+// beta-like parameter), claimed without data (overwrite), or already written
+// by an earlier kernel op (accumulate)
+enum PipeMode { kPipeLoaded = 0, kPipeFresh = 1, kPipeAccumulate = 2 };
+
+struct PipeSource;  // a parsed description
+int pipe_parse(const std::string& text, std::shared_ptr<PipeSource>& out, std::vector<std::string>& operand_names,
+               std::string& why);
+int pipe_compile(const PipeSource& src, std::vector<PipeOperand> operands, const std::map<std::string, double>& vars,
+                 PipeProgram& prog, std::string& why);
 
 // ---------------------------------------------------------- kernel side --
 // Tensor-map encoder (driver entry point fetched at first use).
