@@ -49,13 +49,16 @@ CONFIGS = {
     "potrf-32768": ("potrf", 32768, 32768, 0, 1.0, 0.0, 4 << 30, synth.NORMAL),
     # Section IV nsteps: 4 SUMMA-style calls with 4096-wide panels into one 65536^2 C, Ozaki form, C resident in HBM
     "summa-65536": ("summa", 65536, 65536, 16384, 1.0, 0.5, 48 << 30, synth.NORMAL),
+    # the out-of-core GEMM written in the pipeline-description language, beside the built-in schedule
+    "pipe-16384": ("pipe", 16384, 16384, 16384, 1.5, 0.5, 4 << 30, synth.NORMAL),
 }
 LEVEL3 = ("syrk", "trsm", "potrf")
 # per form: (element dtype name, relative Frobenius tolerance, products per logical product, dtype tag)
 FORMS = {"fp64": ("float64", 1e-13, 1, "f64"), "ozaki": ("float64", 1e-12, 36, "f64 (bf16 digit planes)"),
          "bf16x3": ("float32", 1e-6, 6, "f32 (bf16x3 pieces)"), "batched": ("float64", 1e-13, 1, "f64"),
          "syrk": ("float64", 1e-13, 1, "f64"), "trsm": ("float64", 1e-12, 1, "f64"),
-         "potrf": ("float64", 1e-12, 1, "f64"), "summa": ("float64", 1e-12, 36, "f64 (bf16 digit planes)")}
+         "potrf": ("float64", 1e-12, 1, "f64"), "summa": ("float64", 1e-12, 36, "f64 (bf16 digit planes)"),
+         "pipe": ("float64", 1e-13, 1, "f64")}
 
 
 def batch_shapes(seed, count, lo, hi, cap=64 << 30, es=8):
@@ -940,6 +943,110 @@ def run_summa_bench(args, w, world, rank, local, pg):
     print(json.dumps(line), flush=True)
 
 
+def run_pipe_bench(args, w, world, rank, local, pg):
+    """The MMOOC description of the pipeline language, compiled and run by the library, against
+    ooc_dgemm forced to the same blocking and rings (one call each per step)."""
+    import torch
+    M, N, K = w["M"], w["N"], w["K"]
+    cores = host_cores()
+    A = torch.empty((M, K), dtype=torch.float64, pin_memory=True)
+    B = torch.empty((K, N), dtype=torch.float64, pin_memory=True)
+    C = torch.empty((M, N), dtype=torch.float64, pin_memory=True)
+    for t, s_ in ((A, 0), (B, 1), (C, 2)):
+        synth.fill(t, 600 + rank, s_, w["dist"])
+    flops = 2.0 * M * N * K
+    cfg = config_json(w, "inputs larger than L2: %.0f GiB host operands" % ((M * K + K * N + M * N) * 8 / 2 ** 30))
+    cfg["workload"] = "pipeline-language " + cfg["workload"]
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        run_reference(args, dict(w, form="fp64"), world, rank, pg)
+        return
+    import paper_1808_05056_gb300 as P
+    torch.cuda.set_device(local)
+    P.load()
+    plan = P.ooc_plan(M, N, K, 8, 1, w["budget"], P.make_opts())
+    rings = (plan["depth"], plan["b_buffers"], plan["c_buffers"])
+    pipe = P.Pipe(P.MMOOC_PIPELINE)
+    for name, v in dict(mb=plan["mb"], nb=plan["nb"], kb=plan["kb"], ra=rings[0], rb=rings[1], rc=rings[2],
+                        alpha=w["alpha"], beta=w["beta"], beta_nz=int(w["beta"] != 0.0)).items():
+        pipe.set(name, v)
+    for name, t in (("A", A), ("B", B), ("C", C)):
+        pipe.bind(name, t)
+    opts = P.make_opts(mb=plan["mb"], nb=plan["nb"], kb=plan["kb"], depth=rings[0], b_buffers=rings[1],
+                       c_buffers=rings[2])
+
+    def step_pipe():
+        st = P.ooc_stats()
+        t0 = time.perf_counter()
+        if pipe.run(w["budget"], st) != 0:
+            raise RuntimeError("pipe: %s" % P.ooc_last_error())
+        return st, time.perf_counter() - t0
+
+    def step_native():
+        st = P.ooc_stats()
+        t0 = time.perf_counter()
+        if P.ooc_dgemm("N", "N", M, N, K, w["alpha"], A, K, B, N, w["beta"], C, N, w["budget"], opts, st) != 0:
+            raise RuntimeError("ooc_dgemm: %s" % P.ooc_last_error())
+        return st, time.perf_counter() - t0
+
+    r = 64
+    blocks = sample_blocks(w, 8, r)
+    for _ in range(max(0, args.warmup - 1)):
+        step_pipe()
+    cold = [C[i:i + r, j:j + r].numpy().astype(np.float64) for i, j in blocks]
+    step_pipe()
+    parity = cpu = None
+    if rank == 0:
+        ref, dt, used = oracle_sample(w, A.numpy(), B.numpy(), cold, blocks, r, cores)
+        errs = [float(np.linalg.norm(C[i:i + r, j:j + r].numpy() - rv) / np.linalg.norm(rv))
+                for (i, j), rv in zip(blocks, ref)]
+        parity = {"max_rel_fro": max(errs), "tolerance": 1e-13, "blocks": len(blocks), "block": r,
+                  "pass": max(errs) <= 1e-13}
+        cpu = {"value": 2.0 * r * r * K * len(blocks) / dt / 1e12, "unit": "TFLOP/s", "cores": used,
+               "kind": "oracle", "sample": "%d seeded %dx%d blocks of C, K=%d, %.1f s" % (len(blocks), r, r, K, dt)}
+    clk = ClockSampler(local, enabled=not args.no_clocks)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    runs = [step_pipe() for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    clocks = clk.stop()
+    dev = sum(s_.device_seconds for s_, _ in runs)
+    wall = sum(x for _, x in runs)
+    if pg:
+        import torch.distributed as dist
+        t = torch.tensor([dev, wall], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dev, wall = t.tolist()
+    nat = [step_native() for _ in range(max(1, args.steps))]   # comparison, outside the timed region
+    if rank != 0:
+        return
+    s0 = runs[0][0]
+    pk, pk_src = peaks()
+    peak = pk["bf16_tflops_sustained"] * NOMINAL_FP64_TF / NOMINAL_BF16_TF
+    achieved = flops * args.steps / sum(s_.kernel_seconds for s_, _ in runs) / 1e12
+    line = {
+        "metric": "out-of-core GEMM effective TFLOP/s incl. transfers (pipeline-language schedule)",
+        "value": world * flops * args.steps / dev / 1e12, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * dev / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Philox, pinned host)", "config": cfg,
+        "roofline": {"bound": "tensor", "kernel": "fp64_tile_kernel (FP64 mma.sync, TMA-fed)", "achieved": achieved,
+                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "peak_source": "%s bf16 sustained %.1f TF x nominal FP64/BF16 ratio" % (
+                         pk_src, pk["bf16_tflops_sustained"])},
+        "plan": {"mb": plan["mb"], "nb": plan["nb"], "kb": plan["kb"], "rings": rings},
+        "native_same_plan": {"value": flops * len(nat) / sum(s_.device_seconds for s_, _ in nat) / 1e12,
+                             "unit": "TFLOP/s", "h2d_bytes": nat[0][0].h2d_bytes, "d2h_bytes": nat[0][0].d2h_bytes},
+        "e2e": {"value": world * flops * args.steps / wall / 1e12, "unit": "TFLOP/s",
+                "h2d_bytes_per_step": s0.h2d_bytes, "d2h_bytes_per_step": s0.d2h_bytes},
+        "gpu_launches": s0.kernel_launches, "parity": parity, "cpu_baseline": cpu, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     w = workload(args)
@@ -949,6 +1056,8 @@ def main():
         run_level3_bench(args, w, world, rank, local, pg)
     elif w["form"] == "summa":
         run_summa_bench(args, w, world, rank, local, pg)
+    elif w["form"] == "pipe":
+        run_pipe_bench(args, w, world, rank, local, pg)
     elif w["form"] == "batched":
         run_batched_bench(args, w, world, rank, local, pg)
     elif args.impl == "reference":
