@@ -27,7 +27,7 @@ namespace ooc {
 namespace {
 
 constexpr int kSmall = 64;     // order of the triangular blocks the small kernels take
-constexpr int kVecs = 128;     // right-hand sides per CTA of the substitution kernel
+constexpr int kVecs = 32;      // right-hand sides per CTA of the substitution kernel (one warp: many CTAs)
 
 // Solve Tm x = alpha p for nvec vectors p of n <= 64 elements, where
 // Tm[r][c] = T[c][r] if t_trans else T[r][c], lower or upper triangular (only
@@ -59,14 +59,21 @@ __global__ void __launch_bounds__(kVecs) trsm_small_kernel(const double* __restr
     }
     __syncthreads();
     if (v0 + tid < nvec) {
+        // one right-hand side per thread; four partial sums break the dependent FMA chain
         double* x = Xs[tid];
         for (int q = 0; q < n; ++q) {
             const int r = lower ? q : n - 1 - q;
-            double s = alpha * x[r];
-            if (lower)
-                for (int c = 0; c < r; ++c) s -= Ts[r][c] * x[c];
-            else
-                for (int c = r + 1; c < n; ++c) s -= Ts[r][c] * x[c];
+            const int c0 = lower ? 0 : r + 1, c1 = lower ? r : n;
+            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+            int c = c0;
+            for (; c + 3 < c1; c += 4) {
+                s0 = fma(Ts[r][c], x[c], s0);
+                s1 = fma(Ts[r][c + 1], x[c + 1], s1);
+                s2 = fma(Ts[r][c + 2], x[c + 2], s2);
+                s3 = fma(Ts[r][c + 3], x[c + 3], s3);
+            }
+            for (; c < c1; ++c) s0 = fma(Ts[r][c], x[c], s0);
+            const double s = alpha * x[r] - ((s0 + s1) + (s2 + s3));
             x[r] = unit ? s : s / Ts[r][r];
         }
     }

@@ -377,6 +377,7 @@ int make_plan(const PlanRequest& rq, Plan& p, std::string& why)
     Plan best;
     double best_t = std::numeric_limits<double>::infinity();
     std::vector<Plan>* keep = collect_;  // candidate collection (plan_candidates)
+    std::vector<Plan> tri_pool;          // triangular updates: candidates awaiting the exact estimate
     for (int64_t kb : kbs) {
         const int64_t nkc = rq.K == 0 ? 1 : cdiv(rq.K, kb);
         std::vector<int> nBs = {(int)std::min<int64_t>(2 * nkc, 1 << 20), (int)nkc};
@@ -395,6 +396,17 @@ int make_plan(const PlanRequest& rq, Plan& p, std::string& why)
                             if (c.nR == c.h * c.w) c.nC = 0;       // every block resident: no C ring
                             layout(c, f);
                             if (c.device_bytes > rq.budget) continue;
+                            if (c.tri) {
+                                // triangular updates: rank by the full-update estimate first (the exact
+                                // one walks every block column); the best of these are re-ranked below
+                                Plan full = c;
+                                full.tri = 0;
+                                traffic(full);
+                                full.est_seconds = estimate(full, f, sms, rq.h2d_gbps, rq.d2h_gbps);
+                                c.est_seconds = full.est_seconds;
+                                tri_pool.push_back(c);
+                                continue;
+                            }
                             traffic(c);
                             c.est_seconds = estimate(c, f, sms, rq.h2d_gbps, rq.d2h_gbps);
                             if (keep) keep->push_back(c);
@@ -404,6 +416,21 @@ int make_plan(const PlanRequest& rq, Plan& p, std::string& why)
                                 best = c; best_t = c.est_seconds; found = true;
                             }
                         }
+    }
+    if (!tri_pool.empty()) {
+        const size_t top = std::min<size_t>(tri_pool.size(), 48);
+        std::partial_sort(tri_pool.begin(), tri_pool.begin() + top, tri_pool.end(),
+                          [](const Plan& a, const Plan& b) { return a.est_seconds < b.est_seconds; });
+        for (size_t q = 0; q < top; ++q) {
+            Plan c = tri_pool[q];
+            traffic(c);
+            c.est_seconds = estimate(c, f, sms, rq.h2d_gbps, rq.d2h_gbps);
+            if (keep) keep->push_back(c);
+            if (!found || c.est_seconds < best_t * (1 - 1e-9) ||
+                (c.est_seconds <= best_t * (1 + 1e-9) && c.device_bytes < best.device_bytes)) {
+                best = c; best_t = c.est_seconds; found = true;
+            }
+        }
     }
     if (!found) {
         why = "budget of " + std::to_string(rq.budget) + " bytes is below the smallest plan";
