@@ -27,12 +27,14 @@ namespace ooc {
 namespace {
 
 constexpr int kSmall = 64;     // order of the triangular blocks the small kernels take
-constexpr int kVecs = 32;      // right-hand sides per CTA of the substitution kernel (one warp: many CTAs)
 
 // Solve Tm x = alpha p for nvec vectors p of n <= 64 elements, where
 // Tm[r][c] = T[c][r] if t_trans else T[r][c], lower or upper triangular (only
 // that triangle of the stored T is read), unit diagonal (not read) or not.
-// Element e of vector v lives at P[e * es + v * vs].
+// Element e of vector v lives at P[e * es + v * vs].  kVecs right-hand sides
+// per CTA, one per thread (the launcher picks 128, 64 or 32 so that the grid
+// still fills the SMs).
+template <int kVecs>
 __global__ void __launch_bounds__(kVecs) trsm_small_kernel(const double* __restrict__ T, int64_t ldt, int n,
                                                            int t_trans, int lower, int unit, double* P, int64_t es,
                                                            int64_t vs, int64_t nvec, double alpha)
@@ -138,7 +140,29 @@ __global__ void scale_kernel(double* P, int64_t ld, int64_t rows, int64_t cols, 
     }
 }
 
-constexpr size_t kTrsmSmem = (size_t)(kSmall + kVecs) * (kSmall + 1) * sizeof(double);
+template <int kVecs>
+constexpr size_t trsm_smem() { return (size_t)(kSmall + kVecs) * (kSmall + 1) * sizeof(double); }
+
+template <int kVecs>
+int launch_trsm_small(const double* T, int64_t ldt, int n, bool t_trans, bool lower, bool unit, double* P,
+                      int64_t es, int64_t vs, int64_t nv, cudaStream_t st, std::string& why)
+{
+    static const cudaError_t attr = cudaFuncSetAttribute(
+        trsm_small_kernel<kVecs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem<kVecs>());
+    if (attr != cudaSuccess) {
+        why = std::string("trsm_small_kernel shared memory: ") + cudaGetErrorString(attr);
+        return OOC_ERR_CUDA;
+    }
+    const int64_t grid = (nv + kVecs - 1) / kVecs;
+    trsm_small_kernel<kVecs><<<(unsigned)grid, kVecs, trsm_smem<kVecs>(), st>>>(
+        T, ldt, n, t_trans ? 1 : 0, lower ? 1 : 0, unit ? 1 : 0, P, es, vs, nv, 1.0);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        why = std::string("trsm_small_kernel: ") + cudaGetErrorString(e);
+        return OOC_ERR_CUDA;
+    }
+    return OOC_OK;
+}
 
 int check_launch(const char* what, std::string& why)
 {
@@ -179,17 +203,14 @@ int incore_trsm(bool left, bool op_lower, const double* T, int64_t ldt, bool t_t
         const bool tm_lower = left ? op_lower : !op_lower;
         const bool tm_trans = left ? t_trans : !t_trans;
         const int64_t es = left ? ldp : 1, vs = left ? 1 : ldp;
-        const int64_t grid = (nv + kVecs - 1) / kVecs;
-        static const cudaError_t attr = cudaFuncSetAttribute(
-            trsm_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTrsmSmem);
-        if (attr != cudaSuccess) {
-            why = std::string("trsm_small_kernel shared memory: ") + cudaGetErrorString(attr);
-            return OOC_ERR_CUDA;
-        }
-        trsm_small_kernel<<<(unsigned)grid, kVecs, kTrsmSmem, d.st>>>(T, ldt, (int)n, tm_trans ? 1 : 0, tm_lower ? 1 : 0,
-                                                               unit ? 1 : 0, P, es, vs, nv, 1.0);
+        // the most right-hand sides per CTA (more warps per SM) that still gives two CTAs per SM
+        const int64_t want = 2 * (int64_t)device_sm_count();
         ++d.launches;
-        return check_launch("trsm_small_kernel", why);
+        if ((nv + 127) / 128 >= want)
+            return launch_trsm_small<128>(T, ldt, (int)n, tm_trans, tm_lower, unit, P, es, vs, nv, d.st, why);
+        if ((nv + 63) / 64 >= want)
+            return launch_trsm_small<64>(T, ldt, (int)n, tm_trans, tm_lower, unit, P, es, vs, nv, d.st, why);
+        return launch_trsm_small<32>(T, ldt, (int)n, tm_trans, tm_lower, unit, P, es, vs, nv, d.st, why);
     }
     const int64_t n1 = split_point(n), n2 = n - n1;
     const double* T11 = T;
