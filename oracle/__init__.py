@@ -54,6 +54,8 @@ def load(path=None):
         f.argtypes = blk
     lib.oracle_dtrsm.restype = ctypes.c_int
     lib.oracle_dtrsm.argtypes = [ctypes.c_char] * 4 + [i64, i64, dbl, vp, i64, vp, i64, ctypes.c_int]
+    lib.oracle_dgetrf.restype = i64
+    lib.oracle_dgetrf.argtypes = [i64, vp, i64, vp, ctypes.c_int]
     lib.oracle_dpotrf.restype = i64
     lib.oracle_dpotrf.argtypes = [ctypes.c_char, i64, vp, i64, ctypes.c_int]
     lib.oracle_dgemm.restype = ctypes.c_int

@@ -1,6 +1,7 @@
 /*
- * CPU FP64 oracle for the triangular solve (TRSM) and the Cholesky
- * factorisation (POTRF) built on the out-of-core GEMM.
+ * CPU FP64 oracle for the triangular solve (TRSM), the LU factorisation with
+ * partial pivoting (GETRF) and the Cholesky factorisation (POTRF) built on the
+ * out-of-core GEMM.
  *
  * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may link, load or
  * call this file: only the tests, the smoke check and the CPU-baseline leg of
@@ -20,6 +21,15 @@
  *         is (alpha b_t - sum over the unknowns already found of coefficient x
  *         unknown) / diagonal coefficient, the sum in ascending index order.
  *
+ *   GETRF A = P L U with partial pivoting (row interchanges), L unit lower
+ *         triangular, U upper triangular, stored over A (L below the diagonal,
+ *         U on and above it).  Right-looking, column by column: for j = 0 ..
+ *         n-1 the pivot is the first row p >= j with the largest |a[p][j]|;
+ *         rows j and p are exchanged across all n columns and ipiv[j] = p;
+ *         then a[i][j] /= a[j][j] and a[i][k] -= a[i][j] a[j][k] for i, k > j
+ *         (k ascending per row).  A zero pivot skips the division and the
+ *         update of that column and sets info = j + 1 (first one only).
+ *
  *   POTRF uplo 'L': A = L L^T with L lower triangular, positive diagonal,
  *         computed column by column (Cholesky-Crout): for j = 0 .. n-1,
  *           L[j][j] = sqrt(A[j][j] - sum_{k<j} L[j][k]^2),
@@ -30,8 +40,8 @@
  *
  * Storage is row-major (element (r, c) of X is X[r * ldx + c]).  No blocking,
  * no reordering, no fused multiply-add contraction (-ffp-contract=off).  The
- * independent right-hand sides (TRSM) and the rows of one column (POTRF) are
- * split over host threads, which changes no arithmetic.
+ * independent right-hand sides (TRSM) and the rows below the pivot (GETRF,
+ * POTRF) are split over host threads, which changes no arithmetic.
  */
 #include <math.h>
 #include <pthread.h>
@@ -193,6 +203,82 @@ int64_t oracle_dpotrf(char uplo, int64_t n, double* A, int64_t lda, int nthreads
         potrf_col(&jobs[0]);
         for (int t = 1; t <= started; ++t) pthread_join(th[t], NULL);
         for (int t = started + 1; t < nt; ++t) potrf_col(&jobs[t]);
+    }
+    free(th);
+    free(jobs);
+    return info;
+}
+
+/* ----------------------------------------------------------------- GETRF */
+
+typedef struct {
+    int64_t n, j, lda;
+    double* A;
+    int64_t i0, i1; /* rows below the pivot handled by this thread */
+} getrf_job;
+
+static void* getrf_rows(void* q)
+{
+    const getrf_job* p = (const getrf_job*)q;
+    const int64_t j = p->j, n = p->n, lda = p->lda;
+    double* A = p->A;
+    const double d = A[j * lda + j];
+    for (int64_t i = p->i0; i < p->i1; ++i) {
+        const double l = A[i * lda + j] / d;
+        A[i * lda + j] = l;
+        for (int64_t k = j + 1; k < n; ++k) A[i * lda + k] -= l * A[j * lda + k];
+    }
+    return NULL;
+}
+
+int64_t oracle_dgetrf(int64_t n, double* A, int64_t lda, int64_t* ipiv, int nthreads)
+{
+    if (n <= 0) return 0;
+    if (nthreads < 1) nthreads = 1;
+    pthread_t* th = (pthread_t*)calloc((size_t)nthreads, sizeof(pthread_t));
+    getrf_job* jobs = (getrf_job*)calloc((size_t)nthreads, sizeof(getrf_job));
+    if (!th || !jobs) {
+        free(th);
+        free(jobs);
+        return -1;
+    }
+    int64_t info = 0;
+    for (int64_t j = 0; j < n; ++j) {
+        int64_t p = j;
+        double best = fabs(A[j * lda + j]);
+        for (int64_t i = j + 1; i < n; ++i) {
+            const double v = fabs(A[i * lda + j]);
+            if (v > best) {
+                best = v;
+                p = i;
+            }
+        }
+        ipiv[j] = p;
+        if (p != j)
+            for (int64_t k = 0; k < n; ++k) {
+                const double t = A[j * lda + k];
+                A[j * lda + k] = A[p * lda + k];
+                A[p * lda + k] = t;
+            }
+        if (best == 0.0) {
+            if (!info) info = j + 1;
+            continue;
+        }
+        const int64_t rows = n - j - 1;
+        int nt = nthreads;
+        if ((int64_t)nt > rows / 64) nt = (int)(rows / 64);
+        if (nt < 1) nt = 1;
+        for (int t = 0; t < nt; ++t) {
+            getrf_job jb = {n, j, lda, A, j + 1 + rows * t / nt, j + 1 + rows * (t + 1) / nt};
+            jobs[t] = jb;
+        }
+        int started = 0;
+        for (int t = 1; t < nt; ++t)
+            if (pthread_create(&th[t], NULL, getrf_rows, &jobs[t]) == 0) started = t;
+            else break;
+        getrf_rows(&jobs[0]);
+        for (int t = 1; t <= started; ++t) pthread_join(th[t], NULL);
+        for (int t = started + 1; t < nt; ++t) getrf_rows(&jobs[t]);
     }
     free(th);
     free(jobs);

@@ -13,6 +13,7 @@ definition:
   syrk(uplo, ...)   gemmt with op(B) = op(A)^T.
   trsm(...)         factor.c: substitution for each right-hand side.
   potrf(...)        factor.c: column-by-column Cholesky.
+  getrf(...)        factor.c: right-looking LU with partial pivoting.
 
 Operands are numpy arrays (row-major, float64; float32 is widened for the
 triangle values of gemmt/syrk).  Each function returns a new array.
@@ -78,3 +79,23 @@ def potrf(uplo, A, nthreads=None, lib=None):
     n = F.shape[0]
     info = lib.oracle_dpotrf(uplo.encode(), n, _ptr(F), _ld(F), _threads(nthreads)) if n else 0
     return F, int(info)
+
+
+def getrf(A, nthreads=None, lib=None):
+    """(factors, ipiv, info): L (unit, below the diagonal) and U (on and above it) of a copy of
+    the square A with A = P L U; ipiv[j] = the row exchanged with row j at step j (0-based)."""
+    lib = lib or load()
+    F = np.array(A, dtype=np.float64, copy=True, order="C")
+    n = F.shape[0]
+    ipiv = np.zeros(max(n, 1), dtype=np.int64)
+    info = lib.oracle_dgetrf(n, _ptr(F), _ld(F), ipiv.ctypes.data, _threads(nthreads)) if n else 0
+    return F, ipiv[:n], int(info)
+
+
+def apply_pivots(X, ipiv):
+    """Rows of X exchanged in order: row j with row ipiv[j] (a copy)."""
+    Y = np.array(X, copy=True)
+    for j, p in enumerate(ipiv):
+        if p != j:
+            Y[[j, p]] = Y[[p, j]]
+    return Y

@@ -103,3 +103,42 @@ def test_planted_mistake_is_caught(tmp_path, name):
     old, new = MUTANTS[name]
     lib = _build_variant(tmp_path, name, old, new)
     assert _pins(lib), "mutant %s passed every pin" % name
+
+
+GETRF_MUTANTS = {
+    "getrf_signed_pivot": ("const double v = fabs(A[i * lda + j]);", "const double v = A[i * lda + j];"),
+    "getrf_last_of_ties": ("if (v > best) {", "if (v >= best) {"),
+    "getrf_swap_right_part_only": ("for (int64_t k = 0; k < n; ++k) {\n                const double t = A[j * lda + k];",
+                                   "for (int64_t k = j; k < n; ++k) {\n                const double t = A[j * lda + k];"),
+    "getrf_no_scaling": ("const double l = A[i * lda + j] / d;", "const double l = A[i * lda + j];"),
+    "getrf_update_from_wrong_row": ("A[i * lda + k] -= l * A[j * lda + k];", "A[i * lda + k] -= l * A[i * lda + k];"),
+}
+
+
+def _getrf_pins(lib):
+    rng = np.random.default_rng(21)
+    n = 10
+    L = np.tril(rng.choice([-0.5, -0.25, 0.0, 0.25, 0.5], size=(n, n)), -1) + np.eye(n)
+    U = np.triu(rng.integers(-3, 4, size=(n, n))).astype(np.float64)
+    U[np.diag_indices(n)] = rng.choice([-8.0, -6.0, 6.0, 8.0], size=n)
+    order = rng.permutation(n)
+    A = np.empty((n, n))
+    A[order] = L @ U                                     # exact: dyadic products of small integers
+    F, ipiv, info = level3.getrf(A, lib=lib)
+    ok = (info == 0 and np.array_equal(np.tril(F, -1) + np.eye(n), L) and np.array_equal(np.triu(F), U)
+          and np.array_equal(level3.apply_pivots(A, ipiv), L @ U))
+    _, ipiv2, _ = level3.getrf(np.array([[2.0, 1.0], [-2.0, 3.0]]), lib=lib)
+    return [] if ok and list(ipiv2) == [0, 1] else ["getrf"]
+
+
+@pytest.mark.parametrize("name", sorted(GETRF_MUTANTS))
+def test_planted_getrf_mistake_is_caught(tmp_path, name):
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    old, new = GETRF_MUTANTS[name]
+    lib = _build_variant(tmp_path, name, old, new)
+    assert _getrf_pins(lib), "mutant %s passed every pin" % name
+
+
+def test_committed_getrf_oracle_passes_the_pins():
+    assert _getrf_pins(oracle.load()) == []

@@ -177,3 +177,53 @@ def test_potrf_residual_on_a_random_spd_matrix():
     assert info == 0
     assert np.linalg.norm(L @ L.T - A) / np.linalg.norm(A) < 1e-14
     assert (np.diag(L) > 0).all()
+
+
+# ---- GETRF (LU with partial pivoting) ------------------------------------
+def _lu_from_factors(rng, n):
+    """A = P L U with dyadic |l| <= 1/2 (unit diagonal) and integer U with a large
+    diagonal: each step's pivot is unique (the row whose l is 1) and every
+    operation is exact in FP64.  Returns A, L, U, the row order of A."""
+    L = np.tril(rng.choice([-0.5, -0.25, 0.0, 0.25, 0.5], size=(n, n)), -1) + np.eye(n)
+    U = np.triu(rng.integers(-3, 4, size=(n, n))).astype(np.float64)
+    U[np.diag_indices(n)] = rng.choice([-8.0, -6.0, 6.0, 8.0], size=n)
+    LU = [[sum(Fraction(L[i, k]) * Fraction(U[k, j]) for k in range(n)) for j in range(n)] for i in range(n)]
+    order = rng.permutation(n)
+    A = np.empty((n, n))
+    for i in range(n):
+        A[order[i]] = [float(x) for x in LU[i]]   # row i of L U sits at row order[i] of A
+    return A, L, U
+
+
+def test_getrf_recovers_exact_factors():
+    rng = np.random.default_rng(21)
+    n = 14
+    A, L, U = _lu_from_factors(rng, n)
+    F, ipiv, info = level3.getrf(A)
+    assert info == 0
+    assert np.array_equal(np.tril(F, -1) + np.eye(n), L)
+    assert np.array_equal(np.triu(F), U)
+    # the exchanges put the rows of A in the order of L U
+    assert np.array_equal(level3.apply_pivots(A, ipiv), L @ U)
+
+
+def test_getrf_closed_forms_ties_and_zero_pivots():
+    F, ipiv, info = level3.getrf(np.array([[1.0, 2.0], [4.0, 4.0]]))
+    assert info == 0 and list(ipiv) == [1, 1]
+    assert np.array_equal(F, [[4.0, 4.0], [0.25, 1.0]])       # l = 1/4, u22 = 2 - 4/4
+    F, ipiv, _ = level3.getrf(np.array([[2.0, 1.0], [-2.0, 3.0]]))
+    assert list(ipiv) == [0, 1]                                # ties go to the first row
+    _, ipiv, info = level3.getrf(np.array([[0.0, 0.0], [0.0, 1.0]]))
+    assert info == 1 and list(ipiv) == [0, 1]                  # zero column: no exchange, info set
+
+
+def test_getrf_residual_and_multiplier_bound_on_random_input():
+    rng = np.random.default_rng(22)
+    n = 300
+    A = rng.standard_normal((n, n))
+    F, ipiv, info = level3.getrf(A)
+    L = np.tril(F, -1) + np.eye(n)
+    U = np.triu(F)
+    assert info == 0
+    assert np.abs(np.tril(F, -1)).max() <= 1.0                  # partial pivoting: |l| <= 1
+    assert np.linalg.norm(level3.apply_pivots(A, ipiv) - L @ U) / np.linalg.norm(A) < 1e-13
