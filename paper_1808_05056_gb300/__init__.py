@@ -126,6 +126,7 @@ def load(path=None):
                                        ctypes.POINTER(i64)]
     lib.ooc_dtrsm.argtypes = [ch, ch, ch, ch, i64, i64, dbl, vp, i64, vp, i64, sz, po, ps]
     lib.ooc_dpotrf.argtypes = [ch, i64, vp, i64, sz, po, ps, ctypes.POINTER(i64)]
+    lib.ooc_dgetrf.argtypes = [i64, vp, i64, vp, sz, po, ps, ctypes.POINTER(i64)]
     sp = ctypes.c_void_p
     lib.ooc_session_create.argtypes = [i64, i64, i64, dbl, vp, i64, sz, po, ctypes.POINTER(sp)]
     lib.ooc_session_step.argtypes = [sp, ch, ch, i64, dbl, vp, i64, vp, i64, ps]
@@ -146,7 +147,7 @@ def load(path=None):
     lib.ooc_last_error.argtypes = []
     lib.ooc_last_error.restype = ctypes.c_char_p
     for f in ("ooc_dgemm", "ooc_sgemm", "ooc_dgemm_device", "ooc_plan", "ooc_schedule", "ooc_query_device",
-              "ooc_dgemmt", "ooc_dsyrk", "ooc_ssyrk", "ooc_schedule_gemmt", "ooc_dtrsm", "ooc_dpotrf",
+              "ooc_dgemmt", "ooc_dsyrk", "ooc_ssyrk", "ooc_schedule_gemmt", "ooc_dtrsm", "ooc_dpotrf", "ooc_dgetrf",
               "ooc_session_create", "ooc_session_step", "ooc_session_finish", "ooc_session_free",
               "ooc_session_query", "ooc_schedule_session", "ooc_pipe_create", "ooc_pipe_set", "ooc_pipe_bind",
               "ooc_pipe_schedule", "ooc_pipe_run", "ooc_pipe_free"):
@@ -343,6 +344,13 @@ def ooc_schedule_session(M, N, K, beta_nonzero, budget, opts, resident_blocks, c
                                                                resident_blocks, call, ctypes.byref(st), buf, cap, n),
                   "ooc_schedule_session")
     return st.as_dict(), ops
+
+
+def ooc_dgetrf(N, A, lda, ipiv, budget, opts=None, stats=None):
+    """C ABI ooc_dgetrf; ipiv: an int64 array of N entries (numpy or tensor); returns (status, info)."""
+    info = ctypes.c_int64(0)
+    rc = load().ooc_dgetrf(N, _ptr(A), lda, _ptr(ipiv), budget, _ref(opts), _ref(stats), ctypes.byref(info))
+    return rc, info.value
 
 
 def ooc_dgemm_batched(descs, budget, opts=None, stats=None):

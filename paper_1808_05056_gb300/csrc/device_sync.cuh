@@ -18,6 +18,7 @@ constexpr int kErrWaitFull = 1;
 constexpr int kErrWaitEmpty = 2;
 constexpr int kErrWaitMma = 3;
 constexpr int kErrWaitAcc = 4;
+constexpr int kErrGridBarrier = 5;
 
 __device__ __forceinline__ uint64_t globaltimer_ns()
 {

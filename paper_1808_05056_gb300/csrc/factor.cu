@@ -19,7 +19,10 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <thread>
+#include <vector>
 
+#include "device_sync.cuh"
 #include "ooc_internal.hpp"
 
 namespace ooc {
@@ -131,6 +134,154 @@ __global__ void __launch_bounds__(256) potrf_small_kernel(double* T, int64_t ldt
     }
 }
 
+// ---- LU with partial pivoting ------------------------------------------------
+constexpr int kLuThreads = 256;
+constexpr int kLuWarps = kLuThreads / 32;
+
+// Barrier across the CTAs of a cooperative launch (all co-resident), bounded:
+// a CTA that waits longer than kWaitLimitNs records kErrGridBarrier and gets
+// false (the caller returns), so a lost arrival ends the kernel with an error.
+// bar[0] counts arrivals, bar[1] is the generation.
+__device__ bool grid_barrier(unsigned* bar, int* err)
+{
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned* gen = bar + 1;
+        const unsigned g = *gen;
+        __threadfence();
+        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            const uint64_t t0 = globaltimer_ns();
+            while (*gen == g) {
+                if (globaltimer_ns() - t0 > kWaitLimitNs) {
+                    atomicCAS(err, 0, kErrGridBarrier);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+// Unblocked LU with partial pivoting of an m x nw panel (nw <= 64), in place,
+// row-major with leading dimension ldp: the first largest |a| of each column
+// at or below the diagonal is the pivot (piv[j] = its row), rows are swapped
+// across the nw columns, the rows below are scaled and updated.  CTA g owns
+// rows [g * rows_per_cta, (g + 1) * rows_per_cta); two grid barriers per
+// column: after the per-CTA pivot candidates, and after every CTA has read the
+// pivot row and row j (before their owners rewrite them).  A zero pivot
+// records gofs + j + 1 in *info (first failure wins) and skips the update.
+__global__ void __launch_bounds__(kLuThreads) narrow_lu_kernel(double* P, int64_t ldp, int64_t m, int nw,
+                                                               int64_t rows_per_cta, int64_t* piv, double* cand_v,
+                                                               int64_t* cand_i, unsigned* bar, int* err,
+                                                               unsigned long long* info, int64_t gofs)
+{
+    __shared__ double prow[kSmall], jrow[kSmall];
+    __shared__ double wv[kLuWarps];
+    __shared__ int64_t wi[kLuWarps];
+    __shared__ int64_t s_p;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t r0 = (int64_t)blockIdx.x * rows_per_cta, r1 = min(m, r0 + rows_per_cta);
+    for (int j = 0; j < nw; ++j) {
+        __syncthreads();
+        // local candidate: largest |a[i][j]| over own rows i >= j, smallest row on ties
+        double bv = -1.0;
+        int64_t bi = INT64_MAX;
+        for (int64_t i = max(r0, (int64_t)j) + tid; i < r1; i += kLuThreads) {
+            const double v = fabs(P[i * ldp + j]);
+            if (v > bv) { bv = v; bi = i; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_down_sync(0xffffffffu, bv, o);
+            const int64_t oi = __shfl_down_sync(0xffffffffu, bi, o);
+            if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+        }
+        if (lane == 0) { wv[warp] = bv; wi[warp] = bi; }
+        __syncthreads();
+        if (tid == 0) {
+            for (int w = 1; w < kLuWarps; ++w)
+                if (wv[w] > bv || (wv[w] == bv && wi[w] < bi)) { bv = wv[w]; bi = wi[w]; }
+            cand_v[blockIdx.x] = bv;
+            cand_i[blockIdx.x] = bi;
+        }
+        if (!grid_barrier(bar, err)) return;
+        // every CTA reduces the candidates the same way: the global first maximum
+        if (tid == 0) {
+            double gv = -1.0;
+            int64_t gi = INT64_MAX;
+            for (unsigned g = 0; g < gridDim.x; ++g) {
+                const double v = cand_v[g];
+                const int64_t i = cand_i[g];
+                if (v > gv || (v == gv && i < gi)) { gv = v; gi = i; }
+            }
+            s_p = gi;
+        }
+        __syncthreads();
+        const int64_t p = s_p;
+        for (int k = tid; k < nw; k += kLuThreads) {
+            prow[k] = P[p * ldp + k];
+            jrow[k] = P[(int64_t)j * ldp + k];
+        }
+        if (blockIdx.x == 0 && tid == 0) piv[j] = p;
+        if (!grid_barrier(bar, err)) return;   // rows j and p are read everywhere before they change
+        const double pv = prow[j];
+        const bool zero = pv == 0.0;
+        if (zero && blockIdx.x == 0 && tid == 0) atomicCAS(info, 0ull, (unsigned long long)(gofs + j + 1));
+        // row j becomes the pivot row (its owner writes it)
+        if (j >= r0 && j < r1)
+            for (int k = tid; k < nw; k += kLuThreads) P[(int64_t)j * ldp + k] = prow[k];
+        // own rows below j, one warp per row; row p starts from the old row j
+        for (int64_t i = max(r0, (int64_t)j + 1) + warp; i < r1; i += kLuWarps) {
+            const bool is_p = i == p;
+            double a0 = 0.0, a1 = 0.0;
+            const int k0 = lane, k1 = lane + 32;
+            if (k0 < nw) a0 = is_p ? jrow[k0] : P[i * ldp + k0];
+            if (k1 < nw) a1 = is_p ? jrow[k1] : P[i * ldp + k1];
+            if (!zero) {
+                // the multiplier a[j] / pivot, held by the lane that owns column j
+                const double aj = __shfl_sync(0xffffffffu, j < 32 ? a0 : a1, j & 31);
+                const double l = aj / pv;
+                if (k0 > j && k0 < nw) a0 = fma(-l, prow[k0], a0);
+                if (k1 > j && k1 < nw) a1 = fma(-l, prow[k1], a1);
+                if (k0 == j) a0 = l;
+                if (k1 == j) a1 = l;
+            }
+            if (k0 < nw) P[i * ldp + k0] = a0;
+            if (k1 < nw) P[i * ldp + k1] = a1;
+        }
+    }
+}
+
+// Row interchanges k <-> piv[k] for k in [k0, k1), in order, over columns [0, ncols) of P
+// (one thread per column).
+__global__ void laswp_kernel(double* P, int64_t ldp, int64_t ncols, const int64_t* piv, int64_t k0, int64_t k1)
+{
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncols; c += (int64_t)gridDim.x * blockDim.x)
+        for (int64_t k = k0; k < k1; ++k) {
+            const int64_t p = piv[k];
+            if (p != k) {
+                const double t = P[k * ldp + c];
+                P[k * ldp + c] = P[p * ldp + c];
+                P[p * ldp + c] = t;
+            }
+        }
+}
+
+__global__ void add_offset_kernel(int64_t* v, int64_t n, int64_t off)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        v[i] += off;
+}
+
 __global__ void scale_kernel(double* P, int64_t ld, int64_t rows, int64_t cols, double alpha)
 {
     const int64_t n = rows * cols;
@@ -178,6 +329,11 @@ struct Dev {
     int* err = nullptr;                  // error word of the tile kernels' bounded waits
     unsigned long long* info = nullptr;  // first failed Cholesky pivot (global column + 1)
     int64_t launches = 0;
+    // LU panel scratch: grid barrier words and per-CTA pivot candidates
+    unsigned* bar = nullptr;
+    double* cand_v = nullptr;
+    int64_t* cand_i = nullptr;
+    int lu_grid = 0;
 };
 
 // Split n > 64 at a multiple of 64 near its middle (keeps sub-blocks 16-byte aligned for TMA).
@@ -281,6 +437,63 @@ int incore_potrf(bool upper, double* T, int64_t ldt, int64_t n, int64_t gofs, De
             return rc;
     }
     return incore_potrf(upper, T22, ldt, n2, gofs + n1, d, why);
+}
+
+int launch_laswp(double* P, int64_t ldp, int64_t ncols, const int64_t* piv, int64_t k0, int64_t k1, Dev& d,
+                 std::string& why)
+{
+    if (ncols <= 0 || k1 <= k0) return OOC_OK;
+    const int64_t grid = std::min<int64_t>((ncols + 255) / 256, 4096);
+    laswp_kernel<<<(unsigned)grid, 256, 0, d.st>>>(P, ldp, ncols, piv, k0, k1);
+    ++d.launches;
+    return check_launch("laswp_kernel", why);
+}
+
+// In device memory: LU with partial pivoting of the m x n panel P (m >= n),
+// recursive halving at multiples of 64 (Toledo's recursive LU): factor the
+// left half, interchange the right half's rows, U12 = L11^{-1} A12, A22 -=
+// L21 U12 on the tile kernel, factor A22, interchange the left half's rows.
+// piv (device, n entries) receives panel-relative pivot rows; gofs is the
+// panel's first global column (for info).
+int panel_lu(double* P, int64_t ldp, int64_t m, int64_t n, int64_t* piv, int64_t gofs, Dev& d, std::string& why)
+{
+    if (n <= kSmall) {
+        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(d.lu_grid, (m + 31) / 32));
+        int64_t rows_per_cta = (m + grid - 1) / grid;
+        unsigned* bar = d.bar;
+        int nw = (int)n;
+        void* args[] = {&P, &ldp, &m, &nw, &rows_per_cta, &piv, &d.cand_v, &d.cand_i, &bar, &d.err, &d.info, &gofs};
+        if (cudaMemsetAsync(d.bar, 0, 2 * sizeof(unsigned), d.st) != cudaSuccess) {
+            why = "barrier reset failed";
+            return OOC_ERR_CUDA;
+        }
+        const cudaError_t e = cudaLaunchCooperativeKernel((const void*)narrow_lu_kernel, dim3((unsigned)grid),
+                                                          dim3(kLuThreads), args, 0, d.st);
+        ++d.launches;
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            why = std::string("narrow_lu_kernel cooperative launch: ") + cudaGetErrorString(e);
+            return OOC_ERR_CUDA;
+        }
+        return OOC_OK;
+    }
+    const int64_t n1 = split_point(n), n2 = n - n1;
+    int rc;
+    if ((rc = panel_lu(P, ldp, m, n1, piv, gofs, d, why))) return rc;
+    if ((rc = launch_laswp(P + n1, ldp, n2, piv, 0, n1, d, why))) return rc;
+    if ((rc = incore_trsm(true, true, P, ldp, false, true, n1, P + n1, ldp, n2, d, why))) return rc;
+    if (m > n1) {
+        ++d.launches;
+        if ((rc = launch_fp64_tile(true, false, m - n1, n2, n1, -1.0, P + n1 * ldp, ldp, P + n1, ldp, 1.0, true,
+                                   P + n1 * ldp + n1, ldp, d.err, d.st, why)))
+            return rc;
+        if ((rc = panel_lu(P + n1 * ldp + n1, ldp, m - n1, n2, piv + n1, gofs + n1, d, why))) return rc;
+        add_offset_kernel<<<1, 256, 0, d.st>>>(piv + n1, n2, n1);
+        ++d.launches;
+        if ((rc = check_launch("add_offset_kernel", why))) return rc;
+        if ((rc = launch_laswp(P, ldp, n1, piv, n1, n, d, why))) return rc;
+    }
+    return OOC_OK;
 }
 
 int64_t round_up64(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
@@ -411,6 +624,32 @@ struct Driver {
     }
 };
 
+// Row interchanges k <-> ipiv[k] for k in [k0, k1), in order, over host columns
+// [c0, c1) of A; the columns are split over host threads (each applies every
+// interchange to its columns, so the order is kept).
+void host_laswp(double* A, int64_t lda, int64_t c0, int64_t c1, const int64_t* ipiv, int64_t k0, int64_t k1)
+{
+    if (c1 <= c0 || k1 <= k0) return;
+    const int64_t ncols = c1 - c0;
+    const int64_t hw = std::max<unsigned>(1u, std::thread::hardware_concurrency());
+    const int nt = (int)std::max<int64_t>(1, std::min<int64_t>({hw, 32, ncols / 64}));
+    auto work = [=](int64_t a, int64_t b) {
+        for (int64_t k = k0; k < k1; ++k) {
+            const int64_t p = ipiv[k];
+            if (p != k) std::swap_ranges(A + k * lda + a, A + k * lda + b, A + p * lda + a);
+        }
+    };
+    std::vector<std::thread> th;
+    int started = 1;
+    try {
+        for (int t = 1; t < nt; ++t, ++started) th.emplace_back(work, c0 + ncols * t / nt, c0 + ncols * (t + 1) / nt);
+    } catch (...) {
+    }
+    work(c0, c0 + ncols / nt);
+    for (int t = started; t < nt; ++t) work(c0 + ncols * t / nt, c0 + ncols * (t + 1) / nt);
+    for (auto& x : th) x.join();
+}
+
 // Panel order for a budget: t x t triangular block plus at least 64 vectors of t.
 int64_t panel_order(int64_t n, size_t budget)
 {
@@ -421,44 +660,16 @@ int64_t panel_order(int64_t n, size_t budget)
     return std::min<int64_t>(t, n);
 }
 
-}  // namespace
-
-}  // namespace ooc
-
-using namespace ooc;
-
-int ooc_dtrsm(char side, char uplo, char transA, char diag, int64_t M, int64_t N, double alpha, const double* A,
-              int64_t lda, double* B, int64_t ldb, size_t device_budget_bytes, const ooc_opts* opts,
-              ooc_stats* stats)
+// The left-looking out-of-core TRSM of ooc_dtrsm in the driver's arena (also
+// the U12 solve of the LU driver).  Arguments as for ooc_dtrsm, already checked.
+int trsm_run(Driver& dr, bool left, char uplo, char transA, char diag, int64_t M, int64_t N, double alpha,
+             const double* A, int64_t lda, double* B, int64_t ldb)
 {
-    if (stats) std::memset(stats, 0, sizeof(*stats));
-    if (!(is_l(side) || is_r(side)) || !(is_l(uplo) || is_u(uplo)) || !(is_n(transA) || is_t(transA)) ||
-        !(is_n(diag) || is_u(diag)))
-        return fail(OOC_ERR_INVALID_ARG, "side, uplo, transA or diag out of range");
-    if (M < 0 || N < 0) return fail(OOC_ERR_INVALID_ARG, "negative dimension");
-    const bool left = is_l(side);
-    const int64_t n = left ? M : N;  // order of A
-    if (lda < std::max<int64_t>(1, n) || ldb < std::max<int64_t>(1, N))
-        return fail(OOC_ERR_INVALID_ARG, "leading dimension below the row width");
-    if (M == 0 || N == 0) return OOC_OK;
-    if (!A || !B) return fail(OOC_ERR_INVALID_ARG, "null operand pointer");
     std::string why;
-    int rc = device_check(why);
-    if (rc) return fail(rc, why);
-    if (!host_range_pinned(A, n, n, lda, 8) || !host_range_pinned(B, M, N, ldb, 8))
-        return fail(OOC_ERR_NOT_PINNED, "host operands must be page-locked (cudaHostAlloc / cudaHostRegister)");
-    const int64_t t = panel_order(n, device_budget_bytes);
+    int rc = OOC_OK;
+    const int64_t n = left ? M : N;
+    const int64_t t = panel_order(n, dr.bytes);
     const int64_t ldt = round_up64(t, 16);
-    if ((size_t)(t * ldt * 8 + 256 + 64 * ldt * 8 + 4096) > device_budget_bytes)
-        return fail(OOC_ERR_BUDGET, "budget below one 64 x 64 triangular block and its right-hand sides");
-    Driver dr;
-    if ((rc = dr.init(device_budget_bytes, opts, why))) return fail(rc, why);
-    if (alpha == 0.0) {
-        // X = 0 without reading B (the BLAS rule for alpha == 0)
-        for (int64_t r = 0; r < M; ++r) std::memset(B + r * ldb, 0, (size_t)N * 8);
-        dr.finish(stats, 0.0);
-        return OOC_OK;
-    }
     const bool trans = is_t(transA), unit = is_u(diag);
     const bool op_lower = is_l(uplo) != trans;
     const bool forward = left ? op_lower : !op_lower;  // the coupled unknowns come first
@@ -507,6 +718,48 @@ int ooc_dtrsm(char side, char uplo, char transA, char diag, int64_t M, int64_t N
             if ((rc = dr.drain())) return rc;
         }
     }
+    return OOC_OK;
+}
+
+}  // namespace
+
+}  // namespace ooc
+
+using namespace ooc;
+
+int ooc_dtrsm(char side, char uplo, char transA, char diag, int64_t M, int64_t N, double alpha, const double* A,
+              int64_t lda, double* B, int64_t ldb, size_t device_budget_bytes, const ooc_opts* opts,
+              ooc_stats* stats)
+{
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    if (!(is_l(side) || is_r(side)) || !(is_l(uplo) || is_u(uplo)) || !(is_n(transA) || is_t(transA)) ||
+        !(is_n(diag) || is_u(diag)))
+        return fail(OOC_ERR_INVALID_ARG, "side, uplo, transA or diag out of range");
+    if (M < 0 || N < 0) return fail(OOC_ERR_INVALID_ARG, "negative dimension");
+    const bool left = is_l(side);
+    const int64_t n = left ? M : N;  // order of A
+    if (lda < std::max<int64_t>(1, n) || ldb < std::max<int64_t>(1, N))
+        return fail(OOC_ERR_INVALID_ARG, "leading dimension below the row width");
+    if (M == 0 || N == 0) return OOC_OK;
+    if (!A || !B) return fail(OOC_ERR_INVALID_ARG, "null operand pointer");
+    std::string why;
+    int rc = device_check(why);
+    if (rc) return fail(rc, why);
+    if (!host_range_pinned(A, n, n, lda, 8) || !host_range_pinned(B, M, N, ldb, 8))
+        return fail(OOC_ERR_NOT_PINNED, "host operands must be page-locked (cudaHostAlloc / cudaHostRegister)");
+    const int64_t t = panel_order(n, device_budget_bytes);
+    const int64_t ldt = round_up64(t, 16);
+    if ((size_t)(t * ldt * 8 + 256 + 64 * ldt * 8 + 4096) > device_budget_bytes)
+        return fail(OOC_ERR_BUDGET, "budget below one 64 x 64 triangular block and its right-hand sides");
+    Driver dr;
+    if ((rc = dr.init(device_budget_bytes, opts, why))) return fail(rc, why);
+    if (alpha == 0.0) {
+        // X = 0 without reading B (the BLAS rule for alpha == 0)
+        for (int64_t r = 0; r < M; ++r) std::memset(B + r * ldb, 0, (size_t)N * 8);
+        dr.finish(stats, 0.0);
+        return OOC_OK;
+    }
+    if ((rc = trsm_run(dr, left, uplo, transA, diag, M, N, alpha, A, lda, B, ldb))) return rc;
     dr.finish(stats, left ? (double)M * M * N : (double)M * N * N);
     return OOC_OK;
 }
@@ -579,5 +832,74 @@ int ooc_dpotrf(char uplo, int64_t N, double* A, int64_t lda, size_t device_budge
         }
     }
     dr.finish(stats, (double)N * N * N / 3.0);
+    return OOC_OK;
+}
+
+int ooc_dgetrf(int64_t N, double* A, int64_t lda, int64_t* ipiv, size_t device_budget_bytes, const ooc_opts* opts,
+               ooc_stats* stats, int64_t* info)
+{
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    if (info) *info = 0;
+    if (N < 0 || lda < std::max<int64_t>(1, N)) return fail(OOC_ERR_INVALID_ARG, "bad order or leading dimension");
+    if (N == 0) return OOC_OK;
+    if (!A || !ipiv || !info) return fail(OOC_ERR_INVALID_ARG, "null matrix, pivot or info pointer");
+    std::string why;
+    int rc = device_check(why);
+    if (rc) return fail(rc, why);
+    if (!host_range_pinned(A, N, N, lda, 8))
+        return fail(OOC_ERR_NOT_PINNED, "host operands must be page-locked (cudaHostAlloc / cudaHostRegister)");
+    // panel width: the whole N x t panel, its pivots and the candidates in the arena
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, narrow_lu_kernel, kLuThreads, 0);
+    const int lu_grid = std::max(1, std::min(occ * device_sm_count(), 304));
+    const size_t fixed = 256 + 4096 + (size_t)lu_grid * 16 + 8 * 1024;
+    auto panel_bytes = [&](int64_t w) { return (size_t)N * round_up64(w, 16) * 8; };
+    auto too_big = [&](int64_t w) {
+        return fixed + panel_bytes(w) > device_budget_bytes ||
+               (size_t)(w * round_up64(w, 16) * 8 + 256 + 64 * 8 * round_up64(w, 16) + 4096) > device_budget_bytes;
+    };
+    // N itself when it fits (up to 1024), else the largest multiple of 64 that fits
+    int64_t t = N <= 1024 ? N : 1024;
+    while (t > kSmall && too_big(t)) t = (t - 1) / kSmall * kSmall;
+    if (too_big(t)) return fail(OOC_ERR_BUDGET, "budget below one N x 64 panel");
+    Driver dr;
+    if ((rc = dr.init(device_budget_bytes, opts, why))) return fail(rc, why);
+    const int64_t ldp = round_up64(t, 16);
+    double* dP = reinterpret_cast<double*>(dr.arena + 256);
+    char* after = dr.arena + 256 + panel_bytes(t);
+    int64_t* dpiv = reinterpret_cast<int64_t*>(after);
+    dr.d.cand_v = reinterpret_cast<double*>(after + 8 * 1024);
+    dr.d.cand_i = reinterpret_cast<int64_t*>(after + 8 * 1024 + (size_t)lu_grid * 8);
+    dr.d.bar = reinterpret_cast<unsigned*>(dr.arena + 16);
+    dr.d.lu_grid = lu_grid;
+    std::vector<int64_t> hpiv((size_t)t);
+    for (int64_t c0 = 0; c0 < N; c0 += t) {
+        const int64_t tk = std::min(t, N - c0), m = N - c0;
+        // 1. the interchanges of the finished panels, on this panel's columns
+        host_laswp(A, lda, c0, c0 + tk, ipiv, 0, c0);
+        if (c0 > 0) {
+            // 2. U12 = L11^{-1} A12 (unit lower L11 of order c0), out of core
+            if ((rc = trsm_run(dr, true, 'L', 'N', 'U', c0, tk, 1.0, A, lda, A + c0, lda))) return rc;
+            // 3. A22 -= L21 U12 over the panel's rows c0.., out of core
+            if ((rc = dr.gemm('N', 'N', m, tk, c0, -1.0, A + c0 * lda, lda, A + c0, lda, 1.0, A + c0 * lda + c0, lda,
+                              0)))
+                return rc;
+        }
+        // 4. the panel in device memory
+        if ((rc = dr.copy_in(dP, ldp, A + c0 * lda + c0, lda, m, tk))) return rc;
+        if ((rc = panel_lu(dP, ldp, m, tk, dpiv, c0, dr.d, why))) return fail(rc, why);
+        if ((rc = dr.copy_out(A + c0 * lda + c0, lda, dP, ldp, m, tk))) return rc;
+        if ((rc = dr.drain())) return rc;
+        if (cudaMemcpy(hpiv.data(), dpiv, (size_t)tk * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return fail(OOC_ERR_CUDA, "pivot read failed");
+        for (int64_t q = 0; q < tk; ++q) ipiv[c0 + q] = c0 + hpiv[q];
+        // 5. the panel's interchanges on the columns to its left
+        host_laswp(A, lda, 0, c0, ipiv, c0, c0 + tk);
+    }
+    unsigned long long hinfo = 0;
+    if (cudaMemcpy(&hinfo, dr.d.info, sizeof(hinfo), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(OOC_ERR_CUDA, "pivot word read failed");
+    *info = (int64_t)hinfo;
+    dr.finish(stats, 2.0 * (double)N * N * N / 3.0);
     return OOC_OK;
 }

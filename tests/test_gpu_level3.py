@@ -280,3 +280,76 @@ def test_dpotrf_reports_the_first_bad_pivot(ooc, bad):
     assert rc == 0, ooc.ooc_last_error()
     _, rinfo = level3.potrf("L", A0)
     assert info == rinfo == bad + 1
+
+
+# ---- LU with partial pivoting ------------------------------------------------------
+def _getrf(ooc, A, budget, opts=None):
+    n = A.shape[0]
+    ipiv = np.zeros(n, dtype=np.int64)
+    st = ooc.ooc_stats()
+    rc, info = ooc.ooc_dgetrf(n, A, n, ipiv, budget, opts, st)
+    assert rc == 0, ooc.ooc_last_error()
+    return ipiv, info, st
+
+
+def test_dgetrf_exact_factors_several_panels(ooc):
+    """A = P L U with dyadic |l| <= 1/2 and an integer U: unique pivots, exact arithmetic."""
+    rng = np.random.default_rng(31)
+    n = 300
+    L = np.tril(rng.choice([-0.5, -0.25, 0.0, 0.25, 0.5], size=(n, n)), -1) + np.eye(n)
+    U = np.triu(rng.integers(-3, 4, size=(n, n))).astype(np.float64)
+    U[np.diag_indices(n)] = rng.choice([-8.0, -6.0, 6.0, 8.0], size=n)
+    A = pinned(n, n)
+    A.numpy()[rng.permutation(n)] = L @ U      # dyadic products of small integers: exact
+    A0 = np64(A)
+    ipiv, info, st = _getrf(ooc, A, 256 << 10)   # 64-column panels
+    assert info == 0 and st.steps >= 4
+    F, rpiv, rinfo = level3.getrf(A0)
+    assert list(ipiv) == list(rpiv)
+    assert np.array_equal(np64(A), F)
+    assert np.array_equal(np.triu(np64(A)), U)
+
+
+@pytest.mark.parametrize("n,budget", [(500, 256 << 10), (1500, 4 << 20), (1100, 64 << 20)])
+def test_dgetrf_matches_oracle(ooc, n, budget):
+    A = pinned_from(160 + n, 0, n, n, synth.NORMAL)
+    A0 = np64(A)
+    ipiv, info, _ = _getrf(ooc, A, budget)
+    F, rpiv, rinfo = level3.getrf(A0)
+    assert info == rinfo == 0
+    assert list(ipiv) == list(rpiv)              # clear-cut pivots on these seeded inputs
+    assert oracle.rel_fro(np64(A), F) <= 1e-12
+    got = np64(A)
+    Lg = np.tril(got, -1) + np.eye(n)
+    assert np.abs(np.tril(got, -1)).max() <= 1.0
+    assert oracle.rel_fro(Lg @ np.triu(got), level3.apply_pivots(A0, ipiv)) <= 1e-14
+
+
+def test_dgetrf_ozaki_updates(ooc):
+    n = 1500
+    A = pinned_from(170, 0, n, n, synth.NORMAL)
+    A0 = np64(A)
+    ipiv, info, st = _getrf(ooc, A, 4 << 20, ooc.make_opts(form=ooc.OOC_FORM_OZAKI))
+    F, rpiv, _ = level3.getrf(A0)
+    assert list(ipiv) == list(rpiv)
+    assert oracle.rel_fro(np64(A), F) <= 1e-12
+
+
+@pytest.mark.parametrize("zero_col", [5, 70, 299])
+def test_dgetrf_zero_pivot_sets_info(ooc, zero_col):
+    n = 300
+    A = pinned_from(171, 0, n, n, synth.NORMAL)
+    A.numpy()[:, zero_col] = 0.0   # a zero column stays exactly zero through the elimination
+    A0 = np64(A)
+    ipiv, info, _ = _getrf(ooc, A, 256 << 10)
+    F, rpiv, rinfo = level3.getrf(A0)
+    assert info == rinfo == zero_col + 1
+    assert list(ipiv) == list(rpiv)
+    assert oracle.rel_fro(np64(A), F) <= 1e-12
+
+
+def test_dgetrf_bad_arguments(ooc):
+    A = pinned(8, 8)
+    ipiv = np.zeros(8, dtype=np.int64)
+    assert ooc.ooc_dgetrf(8, A, 4, ipiv, 1 << 20)[0] == ooc.OOC_ERR_INVALID_ARG
+    assert ooc.ooc_dgetrf(8, A, 8, ipiv, 1024)[0] == ooc.OOC_ERR_BUDGET
