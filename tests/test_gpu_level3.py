@@ -310,7 +310,7 @@ def test_dgetrf_exact_factors_several_panels(ooc):
     assert np.array_equal(np.triu(np64(A)), U)
 
 
-@pytest.mark.parametrize("n,budget", [(500, 256 << 10), (1500, 4 << 20), (1100, 64 << 20)])
+@pytest.mark.parametrize("n,budget", [(500, 512 << 10), (1500, 4 << 20), (1100, 64 << 20)])
 def test_dgetrf_matches_oracle(ooc, n, budget):
     A = pinned_from(160 + n, 0, n, n, synth.NORMAL)
     A0 = np64(A)
