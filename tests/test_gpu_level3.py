@@ -329,7 +329,8 @@ def test_dgetrf_ozaki_updates(ooc):
     n = 1500
     A = pinned_from(170, 0, n, n, synth.NORMAL)
     A0 = np64(A)
-    ipiv, info, st = _getrf(ooc, A, 4 << 20, ooc.make_opts(form=ooc.OOC_FORM_OZAKI))
+    # Ozaki operand slots hold whole-K bf16 digit planes: a budget with room for them
+    ipiv, info, st = _getrf(ooc, A, 64 << 20, ooc.make_opts(form=ooc.OOC_FORM_OZAKI))
     F, rpiv, _ = level3.getrf(A0)
     assert list(ipiv) == list(rpiv)
     assert oracle.rel_fro(np64(A), F) <= 1e-12
