@@ -333,7 +333,12 @@ def test_dgetrf_ozaki_updates(ooc):
     ipiv, info, st = _getrf(ooc, A, 64 << 20, ooc.make_opts(form=ooc.OOC_FORM_OZAKI))
     F, rpiv, _ = level3.getrf(A0)
     assert list(ipiv) == list(rpiv)
-    assert oracle.rel_fro(np64(A), F) <= 1e-12
+    got = np64(A)
+    # backward error at FP64 level; the factors themselves carry the Ozaki digits' 2^-48
+    # relative rounding of each update, amplified by the Schur complements' cancellation
+    resid = oracle.rel_fro((np.tril(got, -1) + np.eye(n)) @ np.triu(got), level3.apply_pivots(A0, ipiv))
+    assert resid <= 1e-12
+    assert oracle.rel_fro(got, F) <= 1e-10
 
 
 @pytest.mark.parametrize("zero_col", [5, 70, 299])
