@@ -47,17 +47,18 @@ CONFIGS = {
     "syrk-32768": ("syrk", 32768, 32768, 16384, 1.0, 0.5, 4 << 30, synth.NORMAL),
     "trsm-32768": ("trsm", 32768, 32768, 0, 1.0, 0.0, 4 << 30, synth.UNIFORM),
     "potrf-32768": ("potrf", 32768, 32768, 0, 1.0, 0.0, 4 << 30, synth.NORMAL),
+    "getrf-32768": ("getrf", 32768, 32768, 0, 1.0, 0.0, 4 << 30, synth.NORMAL),
     # Section IV nsteps: 4 SUMMA-style calls with 4096-wide panels into one 65536^2 C, Ozaki form, C resident in HBM
     "summa-65536": ("summa", 65536, 65536, 16384, 1.0, 0.5, 48 << 30, synth.NORMAL),
     # the out-of-core GEMM written in the pipeline-description language, beside the built-in schedule
     "pipe-16384": ("pipe", 16384, 16384, 16384, 1.5, 0.5, 4 << 30, synth.NORMAL),
 }
-LEVEL3 = ("syrk", "trsm", "potrf")
+LEVEL3 = ("syrk", "trsm", "potrf", "getrf")
 # per form: (element dtype name, relative Frobenius tolerance, products per logical product, dtype tag)
 FORMS = {"fp64": ("float64", 1e-13, 1, "f64"), "ozaki": ("float64", 1e-12, 36, "f64 (bf16 digit planes)"),
          "bf16x3": ("float32", 1e-6, 6, "f32 (bf16x3 pieces)"), "batched": ("float64", 1e-13, 1, "f64"),
          "syrk": ("float64", 1e-13, 1, "f64"), "trsm": ("float64", 1e-12, 1, "f64"),
-         "potrf": ("float64", 1e-12, 1, "f64"), "summa": ("float64", 1e-12, 36, "f64 (bf16 digit planes)"),
+         "potrf": ("float64", 1e-12, 1, "f64"), "getrf": ("float64", 1e-12, 1, "f64"), "summa": ("float64", 1e-12, 36, "f64 (bf16 digit planes)"),
          "pipe": ("float64", 1e-13, 1, "f64")}
 
 
@@ -553,6 +554,8 @@ def level3_flops(w):
         return float(n) * (n + 1) * w["K"]
     if w["form"] == "trsm":
         return float(n) * n * w["N"]
+    if w["form"] == "getrf":
+        return 2.0 * float(n) ** 3 / 3.0
     return float(n) ** 3 / 3.0
 
 
@@ -583,6 +586,12 @@ def level3_inputs(w, rank, torch):
         B0 = torch.empty_like(B, pin_memory=True)
         B0.copy_(B)
         return dict(A=A, B=B, B0=B0)
+    if w["form"] == "getrf":
+        A = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
+        synth.fill(A, seed, 0, w["dist"])
+        A0 = torch.empty_like(A, pin_memory=True)
+        A0.copy_(A)
+        return dict(A=A, A0=A0, ipiv=np.zeros(n, dtype=np.int64))
     # potrf: symmetric N(0,1) off the diagonal (lower triangle read), diagonal n + N(0,1): SPD, well conditioned
     A = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
     synth.fill(A, seed, 0, w["dist"])
@@ -599,6 +608,8 @@ def level3_call(P, w, ops, opts, st):
         return P.ooc_dsyrk("L", "N", n, K, w["alpha"], ops["A"], K, w["beta"], ops["C"], n, w["budget"], opts, st), 0
     if w["form"] == "trsm":
         return P.ooc_dtrsm("L", "L", "N", "N", n, N, w["alpha"], ops["A"], n, ops["B"], N, w["budget"], opts, st), 0
+    if w["form"] == "getrf":
+        return P.ooc_dgetrf(n, ops["A"], n, ops["ipiv"], w["budget"], opts, st)
     return P.ooc_dpotrf("L", n, ops["A"], n, w["budget"], opts, st)
 
 
@@ -606,7 +617,7 @@ def level3_restore(w, ops):
     """Put back what the previous call overwrote (outside the timed region)."""
     if w["form"] == "trsm":
         ops["B"].copy_(ops["B0"])
-    elif w["form"] == "potrf":
+    elif w["form"] in ("potrf", "getrf"):
         ops["A"].copy_(ops["A0"])
 
 
@@ -636,6 +647,29 @@ def level3_parity(w, ops, before, cores):
         errs = [oracle.rel_fro(got, ref)]
         flops = float(n) * n * len(cols)
         sample = "%d seeded right-hand sides (columns of B) of order %d" % (len(cols), n)
+    elif w["form"] == "getrf":
+        # entries of P A - L U, each scaled by (|L| |U|)_ij: the entrywise backward error
+        a, a0, ipiv = ops["A"].numpy(), ops["A0"].numpy(), ops["ipiv"]
+        rows = np.arange(n)
+        for j, p in enumerate(ipiv):
+            rows[j], rows[p] = rows[p], rows[j]
+        t0 = time.perf_counter()
+        worst, lmax = 0.0, 0.0
+        for (i, j) in before["entries"]:
+            k = min(i, j)
+            l = np.append(a[i, :k], 1.0 if i <= j else a[i, k])   # L[i, 0..k]
+            u = a[:k + 1, j].copy()                                 # U[0..k, j]
+            if i > j:
+                u[k] = a[k, j]
+            lu = float(np.dot(l, u))
+            scale = float(np.dot(np.abs(l), np.abs(u)))
+            worst = max(worst, abs(lu - a0[rows[i], j]) / max(scale, 1e-300))
+            lmax = max(lmax, float(np.abs(a[i, :min(i, n)]).max()) if i > 0 else 0.0)
+        dt = time.perf_counter() - t0
+        errs = [worst] + ([0.0] if lmax <= 1.0 else [float("inf")])
+        flops = 2.0 * n * len(before["entries"])
+        sample = "%d sampled entries of P A - L U (backward error, scaled by |L||U|) and |L| <= 1 on their rows" % (
+            len(before["entries"]))
     else:
         b = before["lead"]
         t0 = time.perf_counter()
@@ -654,7 +688,7 @@ def level3_parity(w, ops, before, cores):
         flops = float(b) ** 3 / 3.0
         sample = "leading %dx%d block factored by the oracle; %d sampled entries of L L^T" % (
             b, b, len(before["entries"]))
-    parity = {"max_rel_fro": max(errs), "tolerance": tol, "pass": max(errs) <= tol}
+    parity = {"max_rel_fro": float(max(errs)), "tolerance": tol, "pass": bool(max(errs) <= tol)}
     cpu = {"value": flops / dt / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
            "sample": sample + ", %.1f s" % dt}
     return parity, cpu
@@ -677,6 +711,8 @@ def level3_snapshot(w, ops):
     if w["form"] == "trsm":
         cols = sorted(set(int(c) for c in rng.integers(0, N, size=6)) | {0, N - 1})
         return {"cols": cols, "B0": ops["B"].numpy()[:, cols].copy()}
+    if w["form"] == "getrf":
+        return {"entries": [(int(rng.integers(0, n)), int(rng.integers(0, n))) for _ in range(64)]}
     b = min(n, 2048)
     ents = []
     for _ in range(64):
@@ -695,7 +731,8 @@ def run_level3_bench(args, w, world, rank, local, pg):
     desc = {"syrk": "SYRK C = A A^T (lower) N=%d K=%d, alpha=%g beta=%g, N(0,1)" % (w["M"], w["K"], w["alpha"],
                                                                                    w["beta"]),
             "trsm": "TRSM L X = B, lower non-unit, M=%d N=%d, diagonally dominant" % (w["M"], w["N"]),
-            "potrf": "Cholesky A = L L^T N=%d, SPD (symmetric N(0,1) + N I)" % w["M"]}[w["form"]]
+            "potrf": "Cholesky A = L L^T N=%d, SPD (symmetric N(0,1) + N I)" % w["M"],
+            "getrf": "LU with partial pivoting P A = L U N=%d, N(0,1)" % w["M"]}[w["form"]]
     cfg = {"workload": "out-of-core " + desc + ", device budget %.2f GiB" % (w["budget"] / 2 ** 30),
            "form": w["form"], "update_form": args.form or "fp64", "device_budget_bytes": w["budget"],
            "l2": "inputs larger than L2: host operands of %d GiB streamed through the device budget" % (
