@@ -17,6 +17,8 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <thread>
@@ -873,18 +875,32 @@ int ooc_dgetrf(int64_t N, double* A, int64_t lda, int64_t* ipiv, size_t device_b
     dr.d.bar = reinterpret_cast<unsigned*>(dr.arena + 16);
     dr.d.lu_grid = lu_grid;
     std::vector<int64_t> hpiv((size_t)t);
+    // OOC_TRACE=<file>: one line per panel with the host time of each phase (ms)
+    FILE* trace = nullptr;
+    if (const char* tp = std::getenv("OOC_TRACE")) trace = std::fopen(tp, "a");
+    if (trace) std::fprintf(trace, "# getrf N=%lld t=%lld: c0,laswp_right,trsm,gemm,panel,laswp_left\n",
+                            (long long)N, (long long)t);
+    auto now = [] { return std::chrono::steady_clock::now(); };
+    auto ms = [](std::chrono::steady_clock::time_point a, std::chrono::steady_clock::time_point b) {
+        return std::chrono::duration<double, std::milli>(b - a).count();
+    };
     for (int64_t c0 = 0; c0 < N; c0 += t) {
         const int64_t tk = std::min(t, N - c0), m = N - c0;
+        const auto p0 = now();
         // 1. the interchanges of the finished panels, on this panel's columns
         host_laswp(A, lda, c0, c0 + tk, ipiv, 0, c0);
+        const auto p1 = now();
+        auto p2 = p1;
         if (c0 > 0) {
             // 2. U12 = L11^{-1} A12 (unit lower L11 of order c0), out of core
             if ((rc = trsm_run(dr, true, 'L', 'N', 'U', c0, tk, 1.0, A, lda, A + c0, lda))) return rc;
+            p2 = now();
             // 3. A22 -= L21 U12 over the panel's rows c0.., out of core
             if ((rc = dr.gemm('N', 'N', m, tk, c0, -1.0, A + c0 * lda, lda, A + c0, lda, 1.0, A + c0 * lda + c0, lda,
                               0)))
                 return rc;
         }
+        const auto p3 = now();
         // 4. the panel in device memory
         if ((rc = dr.copy_in(dP, ldp, A + c0 * lda + c0, lda, m, tk))) return rc;
         if ((rc = panel_lu(dP, ldp, m, tk, dpiv, c0, dr.d, why))) return fail(rc, why);
@@ -893,9 +909,15 @@ int ooc_dgetrf(int64_t N, double* A, int64_t lda, int64_t* ipiv, size_t device_b
         if (cudaMemcpy(hpiv.data(), dpiv, (size_t)tk * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
             return fail(OOC_ERR_CUDA, "pivot read failed");
         for (int64_t q = 0; q < tk; ++q) ipiv[c0 + q] = c0 + hpiv[q];
+        const auto p4 = now();
         // 5. the panel's interchanges on the columns to its left
         host_laswp(A, lda, 0, c0, ipiv, c0, c0 + tk);
+        const auto p5 = now();
+        if (trace)
+            std::fprintf(trace, "%lld,%.2f,%.2f,%.2f,%.2f,%.2f\n", (long long)c0, ms(p0, p1), ms(p1, p2), ms(p2, p3),
+                         ms(p3, p4), ms(p4, p5));
     }
+    if (trace) std::fclose(trace);
     unsigned long long hinfo = 0;
     if (cudaMemcpy(&hinfo, dr.d.info, sizeof(hinfo), cudaMemcpyDeviceToHost) != cudaSuccess)
         return fail(OOC_ERR_CUDA, "pivot word read failed");
