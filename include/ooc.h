@@ -268,13 +268,12 @@ int ooc_dpotrf(char uplo, int64_t N, double* A, int64_t lda, size_t device_budge
  * place, A = P L U: L unit lower triangular (stored below the diagonal), U
  * upper triangular (on and above it).  ipiv (host, N entries, 0-based): at
  * step j row j was exchanged with row ipiv[j] >= j, applied in order j = 0, 1,
- * ...; the pivot is the first row with the largest |a| in the column.  Left-
- * looking over panels of t columns: the finished panels' interchanges are
- * applied to the panel, its top is solved with the unit lower L11 (out-of-core
- * TRSM), its rows below are updated with one out-of-core GEMM, then the N x t
- * panel is factored in device memory (recursive halving; 64-column panels by
- * one cooperative kernel with a bounded grid barrier per pivot), and its
- * interchanges are applied to the columns on its left.  *info is 0, or j + 1
+ * ...; the pivot is the first row with the largest |a| in the column.  Right-
+ * looking over panels of t columns: the (N - c0) x t panel is factored in
+ * device memory (recursive halving; 64-column panels by one cooperative kernel
+ * with a bounded grid barrier per pivot), its interchanges are applied to the
+ * other columns on the host, U12 = L11^{-1} A12 is solved in device memory,
+ * and the trailing matrix is updated with one out-of-core GEMM.  *info is 0, or j + 1
  * for the first exactly zero pivot (the factorisation still completes, as in
  * LAPACK).  The budget must hold one N x 64 panel.  opts->form: FP64 or Ozaki
  * for the out-of-core updates; same arena rule as ooc_dtrsm.  stats->tflops

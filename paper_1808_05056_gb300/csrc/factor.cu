@@ -857,7 +857,7 @@ int ooc_dgetrf(int64_t N, double* A, int64_t lda, int64_t* ipiv, size_t device_b
     const size_t fixed = 256 + 4096 + (size_t)lu_grid * 16 + 8 * 1024;
     auto panel_bytes = [&](int64_t w) { return (size_t)N * round_up64(w, 16) * 8; };
     auto too_big = [&](int64_t w) {
-        return fixed + panel_bytes(w) > device_budget_bytes ||
+        return fixed + panel_bytes(w) + (size_t)64 * round_up64(w, 16) * 8 + 512 > device_budget_bytes ||
                (size_t)(w * round_up64(w, 16) * 8 + 256 + 64 * 8 * round_up64(w, 16) + 4096) > device_budget_bytes;
     };
     // N itself when it fits (up to 1024), else the largest multiple of 64 that fits
@@ -875,33 +875,25 @@ int ooc_dgetrf(int64_t N, double* A, int64_t lda, int64_t* ipiv, size_t device_b
     dr.d.bar = reinterpret_cast<unsigned*>(dr.arena + 16);
     dr.d.lu_grid = lu_grid;
     std::vector<int64_t> hpiv((size_t)t);
+    // the U12 row panel goes through the arena after the N x t panel, in column chunks
+    const size_t used = 256 + panel_bytes(t) + 8 * 1024 + (size_t)lu_grid * 16;
+    const size_t u_bytes = dr.bytes > used ? dr.bytes - used : 0;
+    double* dU = reinterpret_cast<double*>(dr.arena + ((used + 255) / 256) * 256);
+    const int64_t u_chunk = std::max<int64_t>(16, (int64_t)(u_bytes / (8 * (size_t)round_up64(t, 16)) / 16 * 16) - 16);
     // OOC_TRACE=<file>: one line per panel with the host time of each phase (ms)
     FILE* trace = nullptr;
     if (const char* tp = std::getenv("OOC_TRACE")) trace = std::fopen(tp, "a");
-    if (trace) std::fprintf(trace, "# getrf N=%lld t=%lld: c0,laswp_right,trsm,gemm,panel,laswp_left\n",
-                            (long long)N, (long long)t);
+    if (trace) std::fprintf(trace, "# getrf N=%lld t=%lld: c0,panel,laswp,u12,gemm\n", (long long)N, (long long)t);
     auto now = [] { return std::chrono::steady_clock::now(); };
     auto ms = [](std::chrono::steady_clock::time_point a, std::chrono::steady_clock::time_point b) {
         return std::chrono::duration<double, std::milli>(b - a).count();
     };
+    // Right-looking over panels of t columns: every trailing update is one large
+    // out-of-core GEMM (a full-occupancy output of (N - c0 - t)^2).
     for (int64_t c0 = 0; c0 < N; c0 += t) {
-        const int64_t tk = std::min(t, N - c0), m = N - c0;
+        const int64_t tk = std::min(t, N - c0), m = N - c0, rest = N - c0 - tk;
         const auto p0 = now();
-        // 1. the interchanges of the finished panels, on this panel's columns
-        host_laswp(A, lda, c0, c0 + tk, ipiv, 0, c0);
-        const auto p1 = now();
-        auto p2 = p1;
-        if (c0 > 0) {
-            // 2. U12 = L11^{-1} A12 (unit lower L11 of order c0), out of core
-            if ((rc = trsm_run(dr, true, 'L', 'N', 'U', c0, tk, 1.0, A, lda, A + c0, lda))) return rc;
-            p2 = now();
-            // 3. A22 -= L21 U12 over the panel's rows c0.., out of core
-            if ((rc = dr.gemm('N', 'N', m, tk, c0, -1.0, A + c0 * lda, lda, A + c0, lda, 1.0, A + c0 * lda + c0, lda,
-                              0)))
-                return rc;
-        }
-        const auto p3 = now();
-        // 4. the panel in device memory
+        // 1. the panel A[c0:, c0:c0+tk] (up to date) factored in device memory
         if ((rc = dr.copy_in(dP, ldp, A + c0 * lda + c0, lda, m, tk))) return rc;
         if ((rc = panel_lu(dP, ldp, m, tk, dpiv, c0, dr.d, why))) return fail(rc, why);
         if ((rc = dr.copy_out(A + c0 * lda + c0, lda, dP, ldp, m, tk))) return rc;
@@ -909,13 +901,31 @@ int ooc_dgetrf(int64_t N, double* A, int64_t lda, int64_t* ipiv, size_t device_b
         if (cudaMemcpy(hpiv.data(), dpiv, (size_t)tk * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
             return fail(OOC_ERR_CUDA, "pivot read failed");
         for (int64_t q = 0; q < tk; ++q) ipiv[c0 + q] = c0 + hpiv[q];
-        const auto p4 = now();
-        // 5. the panel's interchanges on the columns to its left
+        const auto p1 = now();
+        // 2. its interchanges on every other column (L to the left, the trailing matrix to the right)
         host_laswp(A, lda, 0, c0, ipiv, c0, c0 + tk);
-        const auto p5 = now();
+        host_laswp(A, lda, c0 + tk, N, ipiv, c0, c0 + tk);
+        const auto p2 = now();
+        // 3. U12 = L11^{-1} A12 in device memory, L11 still in the panel buffer, A12 in column chunks
+        for (int64_t v0 = 0; v0 < rest; v0 += u_chunk) {
+            const int64_t nv = std::min(u_chunk, rest - v0);
+            const int64_t ldu = round_up64(nv, 16);
+            double* hU = A + c0 * lda + c0 + tk + v0;
+            if ((rc = dr.copy_in(dU, ldu, hU, lda, tk, nv))) return rc;
+            if ((rc = incore_trsm(true, true, dP, ldp, false, true, tk, dU, ldu, nv, dr.d, why))) return fail(rc, why);
+            if ((rc = dr.copy_out(hU, lda, dU, ldu, tk, nv))) return rc;
+            if ((rc = dr.drain())) return rc;
+        }
+        const auto p3 = now();
+        // 4. A22 -= L21 U12 over the trailing matrix, out of core
+        if (rest > 0 &&
+            (rc = dr.gemm('N', 'N', rest, rest, tk, -1.0, A + (c0 + tk) * lda + c0, lda, A + c0 * lda + c0 + tk, lda,
+                          1.0, A + (c0 + tk) * lda + c0 + tk, lda, 0)))
+            return rc;
+        const auto p4 = now();
         if (trace)
-            std::fprintf(trace, "%lld,%.2f,%.2f,%.2f,%.2f,%.2f\n", (long long)c0, ms(p0, p1), ms(p1, p2), ms(p2, p3),
-                         ms(p3, p4), ms(p4, p5));
+            std::fprintf(trace, "%lld,%.2f,%.2f,%.2f,%.2f\n", (long long)c0, ms(p0, p1), ms(p1, p2), ms(p2, p3),
+                         ms(p3, p4));
     }
     if (trace) std::fclose(trace);
     unsigned long long hinfo = 0;
