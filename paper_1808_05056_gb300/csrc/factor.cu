@@ -336,7 +336,26 @@ struct Dev {
     double* cand_v = nullptr;
     int64_t* cand_i = nullptr;
     int lu_grid = 0;
+    // Ozaki form for the in-HBM updates: digit-plane scratch (null: FP64 tiles)
+    char* oz = nullptr;
+    size_t oz_bytes = 0;
 };
+
+// One in-HBM update C = alpha op(A) op(B) + beta C: the Ozaki form when the call
+// asked for it and its digit planes fit the scratch, else the FP64 tile kernel.
+int dev_gemm(Dev& d, bool a_k, bool b_k, int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t lda,
+             const double* B, int64_t ldb, double beta, bool read_c, double* C, int64_t ldc, std::string& why,
+             int tri = 0, int64_t tri_off = 0)
+{
+    if (d.oz && K > 0 && ozaki_device_scratch(M, N, K) <= d.oz_bytes) {
+        d.launches += 7;  // two splits of three kernels each, one tensor-core launch
+        return ozaki_gemm_device(a_k, b_k, M, N, K, alpha, A, lda, B, ldb, beta, read_c, C, ldc, d.oz, d.oz_bytes,
+                                 d.err, d.st, why, tri, tri_off);
+    }
+    ++d.launches;
+    return launch_fp64_tile(a_k, b_k, M, N, K, alpha, A, lda, B, ldb, beta, read_c, C, ldc, d.err, d.st, why, tri,
+                            tri_off);
+}
 
 // Split n > 64 at a multiple of 64 near its middle (keeps sub-blocks 16-byte aligned for TMA).
 int64_t split_point(int64_t n) { return std::max<int64_t>(kSmall, (n / 2) / kSmall * kSmall); }
@@ -376,8 +395,7 @@ int incore_trsm(bool left, bool op_lower, const double* T, int64_t ldt, bool t_t
     int rc;
     auto gemm = [&](bool a_k, bool b_k, int64_t M, int64_t N, int64_t K, const double* A, int64_t lda,
                     const double* B, int64_t ldb, double* C) {
-        ++d.launches;
-        return launch_fp64_tile(a_k, b_k, M, N, K, -1.0, A, lda, B, ldb, 1.0, true, C, ldp, d.err, d.st, why);
+        return dev_gemm(d, a_k, b_k, M, N, K, -1.0, A, lda, B, ldb, 1.0, true, C, ldp, why);
     };
     if (left) {
         double* P1 = P;
@@ -424,18 +442,14 @@ int incore_potrf(bool upper, double* T, int64_t ldt, int64_t n, int64_t gofs, De
         double* T21 = T + n1 * ldt;
         if ((rc = incore_trsm(false, false, T, ldt, true, false, n1, T21, ldt, n2, d, why))) return rc;
         // T22 -= L21 L21^T on the lower triangle
-        ++d.launches;
-        if ((rc = launch_fp64_tile(true, true, n2, n2, n1, -1.0, T21, ldt, T21, ldt, 1.0, true, T22, ldt, d.err, d.st,
-                                   why, 1, 0)))
+        if ((rc = dev_gemm(d, true, true, n2, n2, n1, -1.0, T21, ldt, T21, ldt, 1.0, true, T22, ldt, why, 1, 0)))
             return rc;
     } else {
         // U12 = U11^{-T} T12 (left solve with op = transpose of the stored upper U11, a lower op)
         double* T12 = T + n1;
         if ((rc = incore_trsm(true, true, T, ldt, true, false, n1, T12, ldt, n2, d, why))) return rc;
         // T22 -= U12^T U12 on the upper triangle
-        ++d.launches;
-        if ((rc = launch_fp64_tile(false, false, n2, n2, n1, -1.0, T12, ldt, T12, ldt, 1.0, true, T22, ldt, d.err,
-                                   d.st, why, 2, 0)))
+        if ((rc = dev_gemm(d, false, false, n2, n2, n1, -1.0, T12, ldt, T12, ldt, 1.0, true, T22, ldt, why, 2, 0)))
             return rc;
     }
     return incore_potrf(upper, T22, ldt, n2, gofs + n1, d, why);
@@ -485,9 +499,8 @@ int panel_lu(double* P, int64_t ldp, int64_t m, int64_t n, int64_t* piv, int64_t
     if ((rc = launch_laswp(P + n1, ldp, n2, piv, 0, n1, d, why))) return rc;
     if ((rc = incore_trsm(true, true, P, ldp, false, true, n1, P + n1, ldp, n2, d, why))) return rc;
     if (m > n1) {
-        ++d.launches;
-        if ((rc = launch_fp64_tile(true, false, m - n1, n2, n1, -1.0, P + n1 * ldp, ldp, P + n1, ldp, 1.0, true,
-                                   P + n1 * ldp + n1, ldp, d.err, d.st, why)))
+        if ((rc = dev_gemm(d, true, false, m - n1, n2, n1, -1.0, P + n1 * ldp, ldp, P + n1, ldp, 1.0, true,
+                           P + n1 * ldp + n1, ldp, why)))
             return rc;
         if ((rc = panel_lu(P + n1 * ldp + n1, ldp, m - n1, n2, piv + n1, gofs + n1, d, why))) return rc;
         add_offset_kernel<<<1, 256, 0, d.st>>>(piv + n1, n2, n1);
@@ -626,6 +639,32 @@ struct Driver {
     }
 };
 
+// Split a region between a chunk of right-hand sides of a t-order solve (rows:
+// vectors are rows of ld round_up(t, 16); else columns of a t-row block) and,
+// for Ozaki updates, the digit-plane scratch of the largest in-HBM update
+// (order t, the chunk's vectors); sets the Dev's scratch and returns the chunk.
+int64_t chunk_and_scratch(Driver& dr, char* region, size_t region_bytes, int64_t t, bool rows, int64_t nv_max)
+{
+    const int64_t lt = round_up64(t, 16);
+    auto bytes_of = [&](int64_t c) {
+        const size_t b = rows ? (size_t)c * lt * 8 : (size_t)t * round_up64(c, 16) * 8;
+        return (b + 255) / 256 * 256;
+    };
+    int64_t c = rows ? (int64_t)(region_bytes / (8 * (size_t)lt)) : (int64_t)(region_bytes / (8 * (size_t)t)) / 16 * 16;
+    c = std::max<int64_t>(kSmall, std::min(c, round_up64(std::max<int64_t>(nv_max, kSmall), 16)));
+    dr.d.oz = nullptr;
+    dr.d.oz_bytes = 0;
+    if (dr.gemm_opts.form == OOC_FORM_OZAKI) {
+        while (c > kSmall && bytes_of(c) + ozaki_device_scratch(t, c, t) > region_bytes)
+            c = std::max<int64_t>(kSmall, c / 2 / 16 * 16);
+        if (bytes_of(c) + ozaki_device_scratch(t, c, t) <= region_bytes) {
+            dr.d.oz = region + bytes_of(c);
+            dr.d.oz_bytes = region_bytes - bytes_of(c);
+        }
+    }
+    return c;
+}
+
 // Row interchanges k <-> ipiv[k] for k in [k0, k1), in order, over host columns
 // [c0, c1) of A; the columns are split over host threads (each applies every
 // interchange to its columns, so the order is kept).
@@ -699,10 +738,8 @@ int trsm_run(Driver& dr, bool left, char uplo, char transA, char diag, int64_t M
         // the triangular block A_kk (as stored) and the panel in chunks of right-hand sides
         if ((rc = dr.copy_in(dT, ldt, A + r0 * lda + r0, lda, tk, tk))) return rc;
         const int64_t lp = round_up64(left ? 1 : tk, 16);  // leading dimension of a right-side chunk
-        int64_t chunk;
-        if (left) chunk = std::max<int64_t>(kSmall, (int64_t)(p_bytes / (8 * (size_t)tk)) / 16 * 16);
-        else chunk = std::max<int64_t>(kSmall, (int64_t)(p_bytes / (8 * (size_t)lp)));
         const int64_t nv_total = left ? N : M;
+        const int64_t chunk = chunk_and_scratch(dr, reinterpret_cast<char*>(dP), p_bytes, tk, !left, nv_total);
         for (int64_t v0 = 0; v0 < nv_total; v0 += chunk) {
             const int64_t nv = std::min(chunk, nv_total - v0);
             const int64_t ldp = left ? round_up64(nv, 16) : lp;
@@ -801,6 +838,10 @@ int ooc_dpotrf(char uplo, int64_t N, double* A, int64_t lda, size_t device_budge
                 rc = dr.gemm('T', 'N', tk, rest, c0, -1.0, A + c0, lda, A + c0, lda, 1.0, A + c0 * lda + c0, lda, 2);
             if (rc) return rc;
         }
+        // right-hand-side chunks of the panel below (and the Ozaki scratch, also used by the diagonal block)
+        const int64_t nv_total = rest - tk;
+        const int64_t lp = round_up64(tk, 16);
+        const int64_t chunk = chunk_and_scratch(dr, reinterpret_cast<char*>(dP), p_bytes, tk, !upper, nv_total);
         // factor the diagonal block
         double* hD = A + c0 * lda + c0;
         if ((rc = dr.copy_in(dT, ldt, hD, lda, tk, tk))) return rc;
@@ -816,10 +857,6 @@ int ooc_dpotrf(char uplo, int64_t N, double* A, int64_t lda, size_t device_budge
             return OOC_OK;
         }
         // the rest of the panel: X L11^T = P (lower) or U11^T X = P (upper), in chunks
-        const int64_t nv_total = rest - tk;
-        const int64_t lp = round_up64(tk, 16);
-        const int64_t chunk = upper ? std::max<int64_t>(kSmall, (int64_t)(p_bytes / (8 * (size_t)tk)) / 16 * 16)
-                                    : std::max<int64_t>(kSmall, (int64_t)(p_bytes / (8 * (size_t)lp)));
         for (int64_t v0 = 0; v0 < nv_total; v0 += chunk) {
             const int64_t nv = std::min(chunk, nv_total - v0);
             double* hP = upper ? A + c0 * lda + c0 + tk + v0 : A + (c0 + tk + v0) * lda + c0;
@@ -856,14 +893,17 @@ int ooc_dgetrf(int64_t N, double* A, int64_t lda, int64_t* ipiv, size_t device_b
     const int lu_grid = std::max(1, std::min(occ * device_sm_count(), 304));
     const size_t fixed = 256 + 4096 + (size_t)lu_grid * 16 + 8 * 1024;
     auto panel_bytes = [&](int64_t w) { return (size_t)N * round_up64(w, 16) * 8; };
+    const bool oz = opts && opts->form == OOC_FORM_OZAKI;
+    auto oz_of = [&](int64_t w) { return oz ? ozaki_device_scratch(N, w, w) + 256 : (size_t)0; };
     auto too_big = [&](int64_t w) {
-        return fixed + panel_bytes(w) + (size_t)64 * round_up64(w, 16) * 8 + 512 > device_budget_bytes ||
+        return fixed + panel_bytes(w) + oz_of(w) + (size_t)64 * round_up64(w, 16) * 8 + 512 > device_budget_bytes ||
                (size_t)(w * round_up64(w, 16) * 8 + 256 + 64 * 8 * round_up64(w, 16) + 4096) > device_budget_bytes;
     };
     // N itself when it fits (up to 1024), else the largest multiple of 64 that fits
     int64_t t = N <= 1024 ? N : 1024;
     while (t > kSmall && too_big(t)) t = (t - 1) / kSmall * kSmall;
     if (too_big(t)) return fail(OOC_ERR_BUDGET, "budget below one N x 64 panel");
+    const size_t oz_bytes = oz_of(t) ? oz_of(t) - 256 : 0;
     Driver dr;
     if ((rc = dr.init(device_budget_bytes, opts, why))) return fail(rc, why);
     const int64_t ldp = round_up64(t, 16);
@@ -875,10 +915,16 @@ int ooc_dgetrf(int64_t N, double* A, int64_t lda, int64_t* ipiv, size_t device_b
     dr.d.bar = reinterpret_cast<unsigned*>(dr.arena + 16);
     dr.d.lu_grid = lu_grid;
     std::vector<int64_t> hpiv((size_t)t);
-    // the U12 row panel goes through the arena after the N x t panel, in column chunks
-    const size_t used = 256 + panel_bytes(t) + 8 * 1024 + (size_t)lu_grid * 16;
+    // Ozaki updates: digit-plane scratch for the panel's largest in-HBM update (rows N, order t),
+    // then the U12 row panel in column chunks
+    size_t used = (256 + panel_bytes(t) + 8 * 1024 + (size_t)lu_grid * 16 + 255) / 256 * 256;
+    if (oz_bytes) {
+        dr.d.oz = dr.arena + used;
+        dr.d.oz_bytes = oz_bytes;
+        used += (oz_bytes + 255) / 256 * 256;
+    }
     const size_t u_bytes = dr.bytes > used ? dr.bytes - used : 0;
-    double* dU = reinterpret_cast<double*>(dr.arena + ((used + 255) / 256) * 256);
+    double* dU = reinterpret_cast<double*>(dr.arena + used);
     const int64_t u_chunk = std::max<int64_t>(16, (int64_t)(u_bytes / (8 * (size_t)round_up64(t, 16)) / 16 * 16) - 16);
     // OOC_TRACE=<file>: one line per panel with the host time of each phase (ms)
     FILE* trace = nullptr;

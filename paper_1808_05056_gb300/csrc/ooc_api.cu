@@ -138,6 +138,100 @@ int encode_map_3d_bf16(void* map_out, const void* base, uint64_t inner, uint64_t
     return OOC_OK;
 }
 
+// The Ozaki groups of the tensor-core kernel: digit products (s, t) with
+// s + t <= S + 1, two consecutive t per group so that the group loads the A
+// plane s once; each product's exact FP32 sum is weighted 2^(-beta (s + t)).
+void ozaki_groups(TcProblem& P, int S)
+{
+    int n = 0;
+    for (int s1 = 1; s1 <= S; ++s1)
+        for (int t1 = 1; t1 <= S + 1 - s1; t1 += 2) {
+            TcGroupSpec& g = P.groups[n++];
+            const bool two = t1 + 1 <= S + 1 - s1;
+            g.na = 1; g.nb = two ? 2 : 1; g.np = two ? 2 : 1;
+            g.aplane[0] = s1 - 1;
+            g.bplane[0] = t1 - 1; g.bplane[1] = two ? t1 : 0;
+            g.pa[0] = 0; g.pb[0] = 0;
+            g.pa[1] = 0; g.pb[1] = 1;
+            g.scale_exp = -kOzakiBeta * (s1 + t1);
+            g.scale_exp2 = -kOzakiBeta * (s1 + t1 + 1);
+        }
+    P.ngroups = n;
+}
+
+namespace {
+constexpr int kOzakiSlices = 8;
+size_t al256(size_t x) { return (x + 255) / 256 * 256; }
+int64_t up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+size_t side_bytes(int64_t rows, int64_t k_pad)
+{
+    const int64_t rp = up(std::max<int64_t>(rows, 1), 128);
+    return al256((size_t)kOzakiSlices * rp * k_pad * 2) + al256((size_t)rp * 4) + al256((size_t)rp * 8);
+}
+}  // namespace
+
+size_t ozaki_device_scratch(int64_t M, int64_t N, int64_t K)
+{
+    const int64_t k_pad = up(std::max<int64_t>(K, 1), 64);
+    return side_bytes(M, k_pad) + side_bytes(N, k_pad);
+}
+
+int ozaki_gemm_device(bool a_kmajor, bool b_kmajor, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
+                      int64_t lda, const double* B, int64_t ldb, double beta, bool read_c, double* C, int64_t ldc,
+                      void* scratch, size_t scratch_bytes, int* err, void* stream, std::string& why, int tri,
+                      int64_t tri_off)
+{
+    if (M <= 0 || N <= 0) return OOC_OK;
+    if (K <= 0) return launch_fp64_tile(a_kmajor, b_kmajor, M, N, K, alpha, A, lda, B, ldb, beta, read_c, C, ldc,
+                                        err, stream, why, tri, tri_off);
+    if (ozaki_device_scratch(M, N, K) > scratch_bytes) {
+        why = "Ozaki scratch too small";
+        return OOC_ERR_BUDGET;
+    }
+    const int64_t k_pad = up(K, 64);
+    char* base = static_cast<char*>(scratch);
+    struct Side {
+        const double* X;
+        int64_t rows, sr, sk;
+        char* planes;
+        int* exps;
+        unsigned long long* rowmax;
+        int64_t rows_pad;
+    } side[2];
+    side[0] = {A, M, a_kmajor ? lda : 1, a_kmajor ? 1 : lda, nullptr, nullptr, nullptr, up(M, 128)};
+    side[1] = {B, N, b_kmajor ? ldb : 1, b_kmajor ? 1 : ldb, nullptr, nullptr, nullptr, up(N, 128)};
+    for (auto& sd : side) {
+        sd.planes = base;
+        base += al256((size_t)kOzakiSlices * sd.rows_pad * k_pad * 2);
+        sd.exps = reinterpret_cast<int*>(base);
+        base += al256((size_t)sd.rows_pad * 4);
+        sd.rowmax = reinterpret_cast<unsigned long long*>(base);
+        base += al256((size_t)sd.rows_pad * 8);
+        const int rc = launch_split_ozaki(sd.X, sd.sr, sd.sk, (int)sd.rows, (int)K, (int)sd.rows_pad, (int)k_pad,
+                                          kOzakiSlices, kOzakiBeta, sd.planes, sd.exps, sd.rowmax, stream, why);
+        if (rc) return rc;
+    }
+    TcProblem P;
+    P.M = M; P.N = N; P.k_pad = k_pad;
+    P.chunk = kOzakiChunk;
+    P.a_planes = side[0].planes; P.a_rows_pad = side[0].rows_pad; P.a_nplanes = kOzakiSlices;
+    P.b_planes = side[1].planes; P.b_rows_pad = side[1].rows_pad; P.b_nplanes = kOzakiSlices;
+    ozaki_groups(P, kOzakiSlices);
+    P.row_exp = side[0].exps;
+    P.col_exp = side[1].exps;
+    P.alpha = alpha;
+    P.beta = beta;
+    P.read_c = read_c;
+    P.c_fp32 = false;
+    P.C = C;
+    P.ldc = ldc;
+    P.err = err;
+    P.kblock = 64;
+    P.tri = tri;
+    P.tri_off = tri_off;
+    return launch_tc_terms(P, stream, why);
+}
+
 }  // namespace ooc
 
 using namespace ooc;
@@ -357,22 +451,7 @@ int launch_split_tile(const Plan& p, const Op& op, Exec& x, const Operands& o, i
     P.a_planes = planes[0]; P.a_rows_pad = ra_pad; P.a_nplanes = S;
     P.b_planes = planes[1]; P.b_rows_pad = rb_pad; P.b_nplanes = S;
     if (ozaki) {
-        // digit products (s, t) with s + t <= S + 1, two consecutive t per group
-        // so that the group loads the A plane s once
-        int n = 0;
-        for (int s1 = 1; s1 <= S; ++s1)
-            for (int t1 = 1; t1 <= S + 1 - s1; t1 += 2) {
-                TcGroupSpec& g = P.groups[n++];
-                const bool two = t1 + 1 <= S + 1 - s1;
-                g.na = 1; g.nb = two ? 2 : 1; g.np = two ? 2 : 1;
-                g.aplane[0] = s1 - 1;
-                g.bplane[0] = t1 - 1; g.bplane[1] = two ? t1 : 0;
-                g.pa[0] = 0; g.pb[0] = 0;
-                g.pa[1] = 0; g.pb[1] = 1;
-                g.scale_exp = -kOzakiBeta * (s1 + t1);
-                g.scale_exp2 = -kOzakiBeta * (s1 + t1 + 1);
-            }
-        P.ngroups = n;
+        ozaki_groups(P, S);
         P.row_exp = exps[0];
         P.col_exp = exps[1];
     } else {

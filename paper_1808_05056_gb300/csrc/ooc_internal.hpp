@@ -241,6 +241,15 @@ struct TcProblem {
 };
 
 int tc_max_groups();
+void ozaki_groups(TcProblem& P, int S);
+// C = alpha op(A) op(B) + beta C on device FP64 operands in the Ozaki form (8
+// digit planes per operand in `scratch`, at least ozaki_device_scratch bytes);
+// operand conventions as launch_fp64_tile.
+size_t ozaki_device_scratch(int64_t M, int64_t N, int64_t K);
+int ozaki_gemm_device(bool a_kmajor, bool b_kmajor, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
+                      int64_t lda, const double* B, int64_t ldb, double beta, bool read_c, double* C, int64_t ldc,
+                      void* scratch, size_t scratch_bytes, int* err, void* stream, std::string& why, int tri = 0,
+                      int64_t tri_off = 0);
 int launch_tc_terms(const TcProblem& P, void* stream, std::string& why);
 int launch_split_bf16x3(const float* X, int64_t sr, int64_t sk, int rows, int K, int rows_pad, int k_pad,
                         void* planes, void* stream, std::string& why);
