@@ -406,7 +406,7 @@ int launch_split_tile(const Plan& p, const Op& op, Exec& x, const Operands& o, i
 {
     const bool ozaki = p.form == OOC_FORM_OZAKI;
     const int S = split_planes(p);
-    const int64_t rows = p.rows_of(op.i), cols = p.cols_of(op.j), K = p.K;
+    const int64_t rows = p.rows_of(op.i), cols = p.cols_of(op.j), K = p.K > 0 ? p.k_of(op.kc) : 0;  // this chunk
     const int64_t k_pad = split_k_pad(p);
     const int64_t ra_pad = split_rows_pad(p.mb), rb_pad = split_rows_pad(p.nb);
     int* err = reinterpret_cast<int*>(x.arena);

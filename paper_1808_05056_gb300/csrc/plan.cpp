@@ -357,8 +357,19 @@ int make_plan(const PlanRequest& rq, Plan& p, std::string& why)
     const std::vector<int64_t> mbs = sizes(rq.M, f.tile_m, rq.opts.mb);
     const std::vector<int64_t> nbs = sizes(rq.N, f.tile_n, rq.opts.nb);
     std::vector<int64_t> kbs;
-    if (form != OOC_FORM_FP64) kbs.push_back(std::max<int64_t>(rq.K, 1));  // split forms: whole-K slices
-    else if (rq.opts.kb > 0) kbs.push_back(std::min<int64_t>(rq.opts.kb, std::max<int64_t>(rq.K, 1)));
+    if (form != OOC_FORM_FP64) {
+        // split forms: whole-K slices, or up to 16 K chunks (each chunk is split into digit planes on
+        // its own; BF16x3 rounds C to FP32 once per chunk, so few chunks); chunks let the planner
+        // take full-width, contiguous B rows when a whole-K B slice would be narrow
+        if (rq.opts.kb > 0) kbs.push_back(std::min<int64_t>(rq.opts.kb, std::max<int64_t>(rq.K, 1)));
+        else {
+            kbs.push_back(std::max<int64_t>(rq.K, 1));
+            for (int64_t c : {2, 4, 8, 16}) {
+                const int64_t kb = round_up(cdiv(rq.K, c), 64);
+                if (kb < rq.K && kb >= 256 && std::find(kbs.begin(), kbs.end(), kb) == kbs.end()) kbs.push_back(kb);
+            }
+        }
+    } else if (rq.opts.kb > 0) kbs.push_back(std::min<int64_t>(rq.opts.kb, std::max<int64_t>(rq.K, 1)));
     else {
         kbs.push_back(std::max<int64_t>(rq.K, 1));
         for (int64_t c = 2; c <= 1024 && rq.K > 64; c = c < 8 ? c + 1 : c * 2) {

@@ -132,3 +132,25 @@ def test_forms_on_cta_pairs(ooc, form):
     assert rc == 0, ooc.ooc_last_error()
     ref = oracle.gemm("N", "N", 1.5, np64(A), np64(B), 0.5, C0)
     assert oracle.rel_fro(np64(C), ref) <= (TOL_BF16X3 if fp32 else TOL_OZAKI)
+
+
+@pytest.mark.parametrize("form", [3, 2])
+def test_forms_with_k_chunks(ooc, form):
+    """K streamed in chunks (the last one ragged): each chunk is split on its own and the partial
+    results accumulate in C (FP32 for BF16x3, FP64 for Ozaki)."""
+    fp32 = form == 3
+    dt = torch.float32 if fp32 else torch.float64
+    M, N, K = 300, 260, 1000
+    kind = synth.UNIFORM if fp32 else synth.LOGSPREAD
+    A = pinned_from(45, 0, M, K, kind, dtype=dt)
+    B = pinned_from(45, 1, K, N, kind, dtype=dt)
+    C = pinned_from(45, 2, M, N, kind, dtype=dt)
+    C0 = np64(C)
+    st = ooc.ooc_stats()
+    f = ooc.ooc_sgemm if fp32 else ooc.ooc_dgemm
+    rc = f("N", "N", M, N, K, 1.25, A, K, B, N, 0.5, C, N, 1 << 30, ooc.make_opts(form=form, kb=256, mb=128, nb=128),
+           st)
+    assert rc == 0, ooc.ooc_last_error()
+    assert st.kb == 256 and st.steps == 3 * 3 * 4
+    ref = oracle.gemm("N", "N", 1.25, np64(A), np64(B), 0.5, C0)
+    assert oracle.rel_fro(np64(C), ref) <= (TOL_BF16X3 if fp32 else TOL_OZAKI)
