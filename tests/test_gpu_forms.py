@@ -79,7 +79,7 @@ def test_ozaki_transposes_ragged_spread(ooc, ta, tb):
 def test_ozaki_spread_many_blocks_long_k(ooc):
     got, ref, st = _run(ooc, ooc.OOC_FORM_OZAKI, "N", "N", 700, 600, 9000, 1.0, 0.0, synth.LOGSPREAD,
                         budget=64 << 20)
-    assert st.blocks > 1
+    assert st.steps > 1   # several C blocks or K chunks stream through the budget
     assert oracle.rel_fro(got, ref) <= TOL_OZAKI
 
 
