@@ -80,7 +80,11 @@ NOMINAL_FP64_TF, NOMINAL_BF16_TF = 1.25, 2250.0
 # dominant kernel, from one ncu capture of the configuration's plan (the summary
 # under profiles/ named for the kernel); reported only when a run uses that plan.
 TRAFFIC = {"fp64-32768": {"plan": (2048, 8192, 8192), "bytes": 2.624778e9 + 135.795456e6,
-                          "profile": "profiles/fp64_tile_kernel_traffic_32768.md"}}
+                          "profile": "profiles/fp64_tile_kernel_traffic_32768.md"},
+           "ozaki-65536": {"plan": (7296, 8192, 16384), "bytes": 85.821253e9 + 498.774016e6,
+                           "profile": "profiles/tc_terms_kernel_traffic_65536.md"},
+           "bf16x3-65536": {"plan": (1792, 4096, 65536), "bytes": 4.690504e9 + 70.503680e6,
+                            "profile": "profiles/tc_terms_kernel_traffic_65536.md"}}
 
 
 def parse():
@@ -374,7 +378,10 @@ def run_ours(args, w, world, rank, local, pg):
         achieved = flops * s0.products * args.steps / ker_s / 1e12
         roof = {"bound": "tensor",
                 "kernel": "tc_terms_kernel (tcgen05 bf16 x bf16 -> f32 TMEM, TMA) with its split kernels",
-                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                "traffic_alg_bytes": (s0.slices if w["form"] == "ozaki" else 3) * 2.0 * (s0.mb + s0.nb) * s0.kb +
+                                     (2.0 if w["beta"] != 0 else 1.0) * s0.mb * s0.nb * (4 if w["form"] == "bf16x3" else 8),
+                "traffic_source": tr["profile"] if traffic else None,
                 "flop_count": "2*M*N*K x %d bf16 products per logical product" % s0.products,
                 "peak_source": "%s bf16 sustained (cuBLAS) %.1f TF" % (pk_src, peak),
                 "logical_tflops": flops * args.steps / ker_s / 1e12, "launches_per_step": s0.steps}

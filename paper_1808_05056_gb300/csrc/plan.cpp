@@ -356,17 +356,19 @@ int make_plan(const PlanRequest& rq, Plan& p, std::string& why)
     };
     const std::vector<int64_t> mbs = sizes(rq.M, f.tile_m, rq.opts.mb);
     const std::vector<int64_t> nbs = sizes(rq.N, f.tile_n, rq.opts.nb);
-    std::vector<int64_t> kbs;
+    std::vector<int64_t> kbs, split_chunks;
     if (form != OOC_FORM_FP64) {
-        // split forms: whole-K slices, or up to 16 K chunks (each chunk is split into digit planes on
-        // its own; BF16x3 rounds C to FP32 once per chunk, so few chunks); chunks let the planner
-        // take full-width, contiguous B rows when a whole-K B slice would be narrow
+        // split forms: whole-K slices (measured fastest on GB300 whenever they fit), else up to 16 K
+        // chunks (each chunk is split into digit planes on its own; BF16x3 rounds C to FP32 once
+        // per chunk, so few chunks) -- tried only when no whole-K plan fits the budget
         if (rq.opts.kb > 0) kbs.push_back(std::min<int64_t>(rq.opts.kb, std::max<int64_t>(rq.K, 1)));
         else {
             kbs.push_back(std::max<int64_t>(rq.K, 1));
             for (int64_t c : {2, 4, 8, 16}) {
                 const int64_t kb = round_up(cdiv(rq.K, c), 64);
-                if (kb < rq.K && kb >= 256 && std::find(kbs.begin(), kbs.end(), kb) == kbs.end()) kbs.push_back(kb);
+                if (kb < rq.K && kb >= 256 && std::find(split_chunks.begin(), split_chunks.end(), kb) ==
+                                                  split_chunks.end())
+                    split_chunks.push_back(kb);
             }
         }
     } else if (rq.opts.kb > 0) kbs.push_back(std::min<int64_t>(rq.opts.kb, std::max<int64_t>(rq.K, 1)));
@@ -389,6 +391,11 @@ int make_plan(const PlanRequest& rq, Plan& p, std::string& why)
     double best_t = std::numeric_limits<double>::infinity();
     std::vector<Plan>* keep = collect_;  // candidate collection (plan_candidates)
     std::vector<Plan> tri_pool;          // triangular updates: candidates awaiting the exact estimate
+    for (int pass = 0; pass < 2; ++pass) {
+    if (pass == 1) {
+        if (found || !tri_pool.empty() || split_chunks.empty()) break;
+        kbs = split_chunks;  // no whole-K split plan fits: stream K in chunks
+    }
     for (int64_t kb : kbs) {
         const int64_t nkc = rq.K == 0 ? 1 : cdiv(rq.K, kb);
         std::vector<int> nBs = {(int)std::min<int64_t>(2 * nkc, 1 << 20), (int)nkc};
@@ -427,6 +434,7 @@ int make_plan(const PlanRequest& rq, Plan& p, std::string& why)
                                 best = c; best_t = c.est_seconds; found = true;
                             }
                         }
+    }
     }
     if (!tri_pool.empty()) {
         const size_t top = std::min<size_t>(tri_pool.size(), 48);
