@@ -296,8 +296,7 @@ int ooc_dgetrf(int64_t N, double* A, int64_t lda, int64_t* ipiv, size_t device_b
  *   initial value; the final result is beta * C + sum of the calls' products.
  *   k_hint (0: 4096) is the largest inner dimension a call is planned for: the
  *   resident blocks are chosen so that a call of that K still streams its
- *   operands beside them (FP64 calls with a larger K stream it in chunks;
- *   Ozaki calls then fail with OOC_ERR_BUDGET).  opts->form: FP64 or Ozaki;
+ *   operands beside them (a call with a larger K streams it in chunks).  opts->form: FP64 or Ozaki;
  *   opts->workspace (holding the budget) makes the session allocate nothing.
  *   The session owns one arena of device_budget_bytes and three streams.
  * ooc_session_step: adds alpha * op(A) * op(B) (op(A) M x K, op(B) K x N,
