@@ -227,6 +227,18 @@ def dist_init(args):
     return world, rank, local, pg
 
 
+def max_over_ranks(values, pg):
+    """Element-wise maximum of this rank's timings over all ranks (the values themselves alone)."""
+    if not pg:
+        return list(values)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor(list(values), dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.cpu().tolist()
+
+
 def run_reference(args, w, world, rank, pg):
     """--impl reference: the CPU oracle on a bounded sample of the same workload."""
     if rank != 0:
@@ -345,11 +357,7 @@ def run_ours(args, w, world, rank, local, pg):
     wall_s = sum(wl for _, wl in stats)
     ker_s = sum(s.kernel_seconds for s, _ in stats)
     launches = sum(s.kernel_launches for s, _ in stats)
-    if pg:
-        import torch.distributed as dist
-        t = torch.tensor([dev_s, wall_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dev_s, wall_s = t.tolist()
+    dev_s, wall_s = max_over_ranks([dev_s, wall_s], pg)
     if rank != 0:
         return
     flops = 2.0 * M * N * K
@@ -524,6 +532,7 @@ def run_batched_bench(args, w, world, rank, local, pg):
     dev_s = sum(st.device_seconds for st, _ in stats)
     wall_s = sum(wl for _, wl in stats)
     ker_s = sum(st.kernel_seconds for st, _ in stats)
+    dev_s, wall_s = max_over_ranks([dev_s, wall_s], pg)
     if rank != 0:
         return
     s0 = stats[0][0]
@@ -803,11 +812,7 @@ def run_level3_bench(args, w, world, rank, local, pg):
     clocks = clk.stop()
     wall_s = sum(wl for _, wl in stats)
     ker_s = sum(s.kernel_seconds for s, _ in stats)
-    if pg:
-        import torch.distributed as dist
-        t = torch.tensor([wall_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        wall_s = t.item()
+    wall_s, = max_over_ranks([wall_s], pg)
     if rank != 0:
         return
     s0 = stats[0][0]
@@ -955,11 +960,7 @@ def run_summa_bench(args, w, world, rank, local, pg):
         pg.barrier()
     clocks = clk.stop()
     wall = sum(x[0] for x in runs)
-    if pg:
-        import torch.distributed as dist
-        t = torch.tensor([wall], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        wall = t.item()
+    wall, = max_over_ranks([wall], pg)
     plain_t, plain_h2d, plain_d2h = plain_step()   # comparison, outside the timed region
     if rank != 0:
         return
@@ -1060,11 +1061,7 @@ def run_pipe_bench(args, w, world, rank, local, pg):
     clocks = clk.stop()
     dev = sum(s_.device_seconds for s_, _ in runs)
     wall = sum(x for _, x in runs)
-    if pg:
-        import torch.distributed as dist
-        t = torch.tensor([dev, wall], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dev, wall = t.tolist()
+    dev, wall = max_over_ranks([dev, wall], pg)
     nat = [step_native() for _ in range(max(1, args.steps))]   # comparison, outside the timed region
     if rank != 0:
         return
