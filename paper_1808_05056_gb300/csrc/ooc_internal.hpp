@@ -131,7 +131,7 @@ struct Op {
 
 // Events: ready(s) after a load into slot s, free(s) after a kernel read s,
 // out(s) after the D2H of C slot s, done(s) after the last kernel of C slot s.
-inline int32_t ev_ready(const Plan& p, int32_t s) { return s; }
+inline int32_t ev_ready(const Plan&, int32_t s) { return s; }
 inline int32_t ev_free(const Plan& p, int32_t s) { return p.slots() + s; }
 inline int32_t ev_out(const Plan& p, int32_t s) { return 2 * p.slots() + s; }
 inline int32_t ev_done(const Plan& p, int32_t s) { return 3 * p.slots() + s; }
