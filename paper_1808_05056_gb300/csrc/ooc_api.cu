@@ -352,7 +352,9 @@ struct Exec {
     bool own_arena = false;
     bool own_streams = true;   // false: the streams belong to a session and outlive this call
     cudaStream_t st[3] = {nullptr, nullptr, nullptr};
-    cudaStream_t extra_compute = nullptr;  // second compute stream (batched calls)
+    cudaStream_t extra_compute = nullptr;  // second half's streams (batched calls): compute,
+    cudaStream_t extra_h2d = nullptr;      // host-to-device
+    cudaStream_t extra_d2h = nullptr;      // and device-to-host copies
     cudaStream_t smap[3] = {nullptr, nullptr, nullptr};  // schedule stream id -> stream for the current plan
     int ev_base = 0;           // offset of the current plan's events in ev
     bool time_kernels = true;  // record timing events around tile launches (not inside graph capture)
@@ -382,10 +384,13 @@ struct Exec {
         if (t_begin) cudaEventDestroy(t_begin);
         t_begin = nullptr;
         for (auto& e : t_end) { if (e) cudaEventDestroy(e); e = nullptr; }
-        if (extra_compute) cudaStreamSynchronize(extra_compute);
+        for (auto* e : {&extra_compute, &extra_h2d, &extra_d2h})
+            if (*e) cudaStreamSynchronize(*e);
         for (auto& s : st) { if (s && own_streams) cudaStreamDestroy(s); s = nullptr; }
-        if (extra_compute) cudaStreamDestroy(extra_compute);
-        extra_compute = nullptr;
+        for (auto* e : {&extra_compute, &extra_h2d, &extra_d2h}) {
+            if (*e) cudaStreamDestroy(*e);
+            *e = nullptr;
+        }
         if (own_arena && arena) cudaFree(arena);
         arena = nullptr;
         own_arena = false;
@@ -825,8 +830,12 @@ int run_batched(int32_t count, const ooc_gemm_desc* d, size_t budget, const ooc_
         x.own_arena = true;
     }
     for (auto& st : x.st) CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    // the second half runs on its own three streams: a problem waiting for its half's previous
+    // problem never holds up the other half's copies
     CK(cudaStreamCreateWithFlags(&x.extra_compute, cudaStreamNonBlocking));
-    x.ev.resize(2 * E + 2 + 4, nullptr);  // two event sets, two "half done" events, fork/join
+    CK(cudaStreamCreateWithFlags(&x.extra_h2d, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&x.extra_d2h, cudaStreamNonBlocking));
+    x.ev.resize(2 * E + 2 + 6, nullptr);  // two event sets, two "half done" events, fork + five joins
     for (auto& e : x.ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     x.kev.resize(2 * nkern, nullptr);
     for (auto& e : x.kev) CK(cudaEventCreate(&e));
@@ -843,18 +852,17 @@ int run_batched(int32_t count, const ooc_gemm_desc* d, size_t budget, const ooc_
     if (use_graph) CK(cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal));
     else CK(cudaEventRecord(x.t_begin, s0));
     CK(cudaEventRecord(x.ev[ev_fork], s0));
-    CK(cudaStreamWaitEvent(x.st[kStreamCompute], x.ev[ev_fork], 0));
-    CK(cudaStreamWaitEvent(x.st[kStreamD2H], x.ev[ev_fork], 0));
-    CK(cudaStreamWaitEvent(x.extra_compute, x.ev[ev_fork], 0));
+    cudaStream_t others[5] = {x.st[kStreamCompute], x.st[kStreamD2H], x.extra_compute, x.extra_h2d, x.extra_d2h};
+    for (cudaStream_t o : others) CK(cudaStreamWaitEvent(o, x.ev[ev_fork], 0));
     CK(cudaMemsetAsync(x.arena, 0, sizeof(int), s0));
     bool issued_half[2] = {false, false};
     for (int g = 0; g < count; ++g) {
         if (d[g].M == 0 || d[g].N == 0) continue;
         const int h = g & 1;
         x.base = x.arena + 256 + (size_t)h * half;
-        x.smap[kStreamH2D] = x.st[kStreamH2D];
+        x.smap[kStreamH2D] = h ? x.extra_h2d : x.st[kStreamH2D];
         x.smap[kStreamCompute] = h ? x.extra_compute : x.st[kStreamCompute];
-        x.smap[kStreamD2H] = x.st[kStreamD2H];
+        x.smap[kStreamD2H] = h ? x.extra_d2h : x.st[kStreamD2H];
         x.ev_base = h * E;
         if (issued_half[h]) {
             // the previous problem in this half has copied its last block out
@@ -874,13 +882,13 @@ int run_batched(int32_t count, const ooc_gemm_desc* d, size_t budget, const ooc_
             }
             return rc;
         }
-        CK(cudaEventRecord(x.ev[ev_done0 + h], x.st[kStreamD2H]));
+        CK(cudaEventRecord(x.ev[ev_done0 + h], x.smap[kStreamD2H]));
         issued_half[h] = true;
     }
-    CK(cudaEventRecord(x.ev[ev_fork + 1], x.st[kStreamCompute]));
-    CK(cudaEventRecord(x.ev[ev_fork + 2], x.st[kStreamD2H]));
-    CK(cudaEventRecord(x.ev[ev_fork + 3], x.extra_compute));
-    for (int k = 1; k <= 3; ++k) CK(cudaStreamWaitEvent(s0, x.ev[ev_fork + k], 0));
+    for (int k = 0; k < 5; ++k) {
+        CK(cudaEventRecord(x.ev[ev_fork + 1 + k], others[k]));
+        CK(cudaStreamWaitEvent(s0, x.ev[ev_fork + 1 + k], 0));
+    }
     if (!use_graph) {
         for (auto& e : x.t_end) CK(cudaEventRecord(e, s0));
     } else {
@@ -901,7 +909,7 @@ int run_batched(int32_t count, const ooc_gemm_desc* d, size_t budget, const ooc_
     }
     cudaError_t se = cudaStreamSynchronize(s0);
     for (auto st : x.st) cudaStreamSynchronize(st);
-    cudaStreamSynchronize(x.extra_compute);
+    for (cudaStream_t o : others) cudaStreamSynchronize(o);
     if (gexec) cudaGraphExecDestroy(gexec);
     if (graph) cudaGraphDestroy(graph);
     if (se != cudaSuccess) return fail(OOC_ERR_CUDA, std::string("batched pipeline: ") + cudaGetErrorString(se));
