@@ -20,6 +20,7 @@
 #include <memory>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "ooc_internal.hpp"
@@ -795,20 +796,45 @@ int run_batched(int32_t count, const ooc_gemm_desc* d, size_t budget, const ooc_
     const bool have_link = ooc_query_device(nullptr, &hg, &dg) == OOC_OK && hg > 0 && dg > 0;
     const size_t half = ((budget > 512 ? budget - 256 : 0) / 2) / 256 * 256;
 
-    // plans and schedules, each within half of the budget
+    // plans and schedules, each within half of the budget; the problems are planned in
+    // parallel on host threads (planning is host work: candidate search, cost model)
     std::vector<Plan> plans(count);
     std::vector<std::vector<Op>> sched(count);
+    std::vector<int> prc(count, OOC_OK);
+    std::vector<std::string> pwhy(count);
+    int cur_dev = 0;
+    cudaGetDevice(&cur_dev);
+    auto plan_some = [&](int t, int nt) {
+        cudaSetDevice(cur_dev);  // the cost model runs on the caller's device
+        for (int g = t; g < count; g += nt) {
+            if (d[g].M == 0 || d[g].N == 0) continue;
+            PlanRequest rq{d[g].M, d[g].N, d[g].K, 8, d[g].beta != 0.0, is_t(d[g].transA), is_t(d[g].transB), half,
+                           opts};
+            rq.lda = d[g].lda; rq.ldb = d[g].ldb; rq.ldc = d[g].ldc;
+            if (have_link) { rq.h2d_gbps = hg; rq.d2h_gbps = dg; }
+            prc[g] = make_plan(rq, plans[g], pwhy[g]);
+            if (prc[g] == OOC_OK) build_schedule(plans[g], sched[g]);
+        }
+    };
+    {
+        const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+        const int nt = std::max(1, std::min({hw, 16, count}));
+        std::vector<std::thread> th;
+        int started = 1;
+        try {
+            for (int t = 1; t < nt; ++t, ++started) th.emplace_back(plan_some, t, nt);
+        } catch (...) {
+        }
+        plan_some(0, nt);
+        for (int t = started; t < nt; ++t) plan_some(t, nt);
+        for (auto& x : th) x.join();
+    }
     int E = 0;
     int64_t nkern = 0;
     double flops = 0;
     for (int g = 0; g < count; ++g) {
         if (d[g].M == 0 || d[g].N == 0) continue;
-        PlanRequest rq{d[g].M, d[g].N, d[g].K, 8, d[g].beta != 0.0, is_t(d[g].transA), is_t(d[g].transB), half, opts};
-        rq.lda = d[g].lda; rq.ldb = d[g].ldb; rq.ldc = d[g].ldc;
-        if (have_link) { rq.h2d_gbps = hg; rq.d2h_gbps = dg; }
-        rc = make_plan(rq, plans[g], why);
-        if (rc) return fail(rc, "batched problem " + std::to_string(g) + ": " + why);
-        build_schedule(plans[g], sched[g]);
+        if (prc[g]) return fail(prc[g], "batched problem " + std::to_string(g) + ": " + pwhy[g]);
         E = std::max(E, n_events(plans[g]));
         for (const Op& op : sched[g]) nkern += op.kind == kKernel;
         flops += 2.0 * (double)d[g].M * d[g].N * d[g].K;
