@@ -273,6 +273,12 @@ class Session:
             load().ooc_session_free(self._h)
             self._h = ctypes.c_void_p()
 
+    def __del__(self):
+        try:
+            self.free()   # a session dropped without finish() releases its arena (nothing is written back)
+        except Exception:
+            pass
+
 
 class Pipe:
     """A pipeline description compiled by the library (ooc_pipe_*)."""
