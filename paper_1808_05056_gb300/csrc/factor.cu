@@ -1,17 +1,19 @@
-// Out-of-core triangular solve (TRSM) and Cholesky factorisation (POTRF)
-// built on the out-of-core GEMM -- the step Section VII of the paper names
-// after its DGEMM: the rest of level-3 BLAS and the factorisations that use
-// the out-of-core DGEMM as their building block.
+// Out-of-core triangular solve (TRSM), Cholesky (POTRF) and LU with partial
+// pivoting (GETRF) built on the out-of-core GEMM -- the step Section VII of the
+// paper names after its DGEMM: the rest of level-3 BLAS and the factorisations
+// that use the out-of-core DGEMM as their building block.
 //
-// Both drivers are left-looking over panels of the solution / factor:
+// TRSM and Cholesky are left-looking over panels of the solution / factor:
 //   1. the panel is brought up to date with one out-of-core GEMM (GEMMT with a
 //      triangle mask for Cholesky) over everything already solved, streamed
 //      from host memory by the Section IV pipeline (ooc_api.cu);
 //   2. the panel is solved / factored in device memory by a recursive
 //      blocked algorithm: triangular blocks of at most 64 by the substitution
-//      and Cholesky kernels below, everything else by the FP64 tile kernel.
-// So nearly all flops run in the pipelined GEMM, in the caller's form (FP64
-// tiles, or the FP64-accurate Ozaki tensor-core form).
+//      and Cholesky kernels below, everything else by the tile kernels.
+// LU is right-looking: each panel is factored in device memory (recursive
+// halving down to a cooperative 64-column kernel), then the trailing matrix
+// gets one out-of-core GEMM.  So nearly all flops run in the pipelined GEMM,
+// in the caller's form (FP64 tiles, or the FP64-accurate Ozaki tensor-core form).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -139,6 +141,7 @@ __global__ void __launch_bounds__(256) potrf_small_kernel(double* T, int64_t ldt
 // ---- LU with partial pivoting ------------------------------------------------
 constexpr int kLuThreads = 256;
 constexpr int kLuWarps = kLuThreads / 32;
+constexpr size_t kLuSmemMax = 200 * 1024;  // dynamic shared memory for a CTA's rows
 
 // Barrier across the CTAs of a cooperative launch (all co-resident), bounded:
 // a CTA that waits longer than kWaitLimitNs records kErrGridBarrier and gets
@@ -178,28 +181,59 @@ __device__ bool grid_barrier(unsigned* bar, int* err)
 // row-major with leading dimension ldp: the first largest |a| of each column
 // at or below the diagonal is the pivot (piv[j] = its row), rows are swapped
 // across the nw columns, the rows below are scaled and updated.  CTA g owns
-// rows [g * rows_per_cta, (g + 1) * rows_per_cta); two grid barriers per
-// column: after the per-CTA pivot candidates, and after every CTA has read the
-// pivot row and row j (before their owners rewrite them).  A zero pivot
-// records gofs + j + 1 in *info (first failure wins) and skips the update.
+// rows [g * rows_per_cta, (g + 1) * rows_per_cta) and is the only one that
+// writes them; with kInSmem they stay in shared memory (stride kLuLd) from the
+// first column to the last.  Per column each CTA publishes its candidate
+// (largest |a|, smallest row on ties) together with that row's current
+// values, and the owner of row j publishes row j; one grid barrier; then
+// every CTA picks the same global winner and reads the pivot row and row j
+// from the published copies.  The published slots alternate between two
+// buffers by column parity: a CTA can only rewrite a column's slots two
+// columns later, after the next barrier, which every CTA reaches only when
+// it has finished reading them.  A zero pivot records gofs + j + 1 in *info
+// (first failure wins) and skips the update; a column with no comparable
+// entry (all NaN) keeps row j as its pivot.
+constexpr int kLuLd = kSmall + 1;  // shared-memory row stride (doubles): column reads hit distinct banks
+
+template <bool kInSmem>
+__device__ __forceinline__ double& lu_at(double* S, double* P, int64_t ldp, int64_t r0, int64_t i, int k)
+{
+    if constexpr (kInSmem) return S[(i - r0) * kLuLd + k];
+    else return P[i * ldp + k];
+}
+
+template <bool kInSmem>
 __global__ void __launch_bounds__(kLuThreads) narrow_lu_kernel(double* P, int64_t ldp, int64_t m, int nw,
                                                                int64_t rows_per_cta, int64_t* piv, double* cand_v,
-                                                               int64_t* cand_i, unsigned* bar, int* err,
-                                                               unsigned long long* info, int64_t gofs)
+                                                               int64_t* cand_i, double* cand_row, double* jrow_buf,
+                                                               unsigned* bar, int* err, unsigned long long* info,
+                                                               int64_t gofs)
 {
+    extern __shared__ double S[];  // kInSmem: the CTA's rows
     __shared__ double prow[kSmall], jrow[kSmall];
     __shared__ double wv[kLuWarps];
     __shared__ int64_t wi[kLuWarps];
-    __shared__ int64_t s_p;
+    __shared__ int64_t s_bi, s_p;
+    __shared__ int s_found;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned G = gridDim.x;
     const int64_t r0 = (int64_t)blockIdx.x * rows_per_cta, r1 = min(m, r0 + rows_per_cta);
+    if constexpr (kInSmem) {
+        const int64_t n = (r1 > r0 ? r1 - r0 : 0) * nw;
+        for (int64_t e = tid; e < n; e += kLuThreads) {
+            const int64_t r = e / nw;
+            const int k = (int)(e % nw);
+            S[r * kLuLd + k] = P[(r0 + r) * ldp + k];
+        }
+    }
     for (int j = 0; j < nw; ++j) {
+        const int b = j & 1;
         __syncthreads();
         // local candidate: largest |a[i][j]| over own rows i >= j, smallest row on ties
         double bv = -1.0;
         int64_t bi = INT64_MAX;
         for (int64_t i = max(r0, (int64_t)j) + tid; i < r1; i += kLuThreads) {
-            const double v = fabs(P[i * ldp + j]);
+            const double v = fabs(lu_at<kInSmem>(S, P, ldp, r0, i, j));
             if (v > bv) { bv = v; bi = i; }
         }
         for (int o = 16; o > 0; o >>= 1) {
@@ -212,53 +246,81 @@ __global__ void __launch_bounds__(kLuThreads) narrow_lu_kernel(double* P, int64_
         if (tid == 0) {
             for (int w = 1; w < kLuWarps; ++w)
                 if (wv[w] > bv || (wv[w] == bv && wi[w] < bi)) { bv = wv[w]; bi = wi[w]; }
-            cand_v[blockIdx.x] = bv;
-            cand_i[blockIdx.x] = bi;
+            cand_v[b * G + blockIdx.x] = bv;
+            cand_i[b * G + blockIdx.x] = bi;
+            s_bi = bi;
+        }
+        __syncthreads();
+        // publish the candidate row and, from its owner, row j
+        const int64_t cb = s_bi;
+        double* crow = cand_row + ((int64_t)b * G + blockIdx.x) * kSmall;
+        for (int k = tid; k < nw; k += kLuThreads) {
+            if (cb != INT64_MAX) crow[k] = lu_at<kInSmem>(S, P, ldp, r0, cb, k);
+            if (j >= r0 && j < r1) jrow_buf[b * kSmall + k] = lu_at<kInSmem>(S, P, ldp, r0, j, k);
         }
         if (!grid_barrier(bar, err)) return;
         // every CTA reduces the candidates the same way: the global first maximum
-        if (tid == 0) {
+        if (warp == 0) {
             double gv = -1.0;
             int64_t gi = INT64_MAX;
-            for (unsigned g = 0; g < gridDim.x; ++g) {
-                const double v = cand_v[g];
-                const int64_t i = cand_i[g];
+            for (unsigned g = lane; g < G; g += 32) {
+                const double v = __ldcg(cand_v + b * G + g);
+                const int64_t i = __ldcg(cand_i + b * G + g);
                 if (v > gv || (v == gv && i < gi)) { gv = v; gi = i; }
             }
-            s_p = gi;
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ov = __shfl_down_sync(0xffffffffu, gv, o);
+                const int64_t oi = __shfl_down_sync(0xffffffffu, gi, o);
+                if (ov > gv || (ov == gv && oi < gi)) { gv = ov; gi = oi; }
+            }
+            if (lane == 0) {
+                s_found = gi != INT64_MAX;
+                s_p = gi != INT64_MAX ? gi : (int64_t)j;
+            }
         }
         __syncthreads();
         const int64_t p = s_p;
+        const double* src = s_found ? cand_row + ((int64_t)b * G + (unsigned)(p / rows_per_cta)) * kSmall
+                                    : jrow_buf + b * kSmall;
         for (int k = tid; k < nw; k += kLuThreads) {
-            prow[k] = P[p * ldp + k];
-            jrow[k] = P[(int64_t)j * ldp + k];
+            prow[k] = __ldcg(src + k);
+            jrow[k] = __ldcg(jrow_buf + b * kSmall + k);
         }
         if (blockIdx.x == 0 && tid == 0) piv[j] = p;
-        if (!grid_barrier(bar, err)) return;   // rows j and p are read everywhere before they change
+        __syncthreads();
         const double pv = prow[j];
         const bool zero = pv == 0.0;
         if (zero && blockIdx.x == 0 && tid == 0) atomicCAS(info, 0ull, (unsigned long long)(gofs + j + 1));
-        // row j becomes the pivot row (its owner writes it)
-        if (j >= r0 && j < r1)
-            for (int k = tid; k < nw; k += kLuThreads) P[(int64_t)j * ldp + k] = prow[k];
-        // own rows below j, one warp per row; row p starts from the old row j
+        // the interchange on own rows: row j becomes the pivot row, row p the old row j
+        for (int k = tid; k < nw; k += kLuThreads) {
+            if (j >= r0 && j < r1) lu_at<kInSmem>(S, P, ldp, r0, j, k) = prow[k];
+            if (p != j && p >= r0 && p < r1) lu_at<kInSmem>(S, P, ldp, r0, p, k) = jrow[k];
+        }
+        __syncthreads();
+        if (zero) continue;
+        // own rows below j, one warp per row: multiplier a[j] / pivot, then the rank-1 update
         for (int64_t i = max(r0, (int64_t)j + 1) + warp; i < r1; i += kLuWarps) {
-            const bool is_p = i == p;
-            double a0 = 0.0, a1 = 0.0;
             const int k0 = lane, k1 = lane + 32;
-            if (k0 < nw) a0 = is_p ? jrow[k0] : P[i * ldp + k0];
-            if (k1 < nw) a1 = is_p ? jrow[k1] : P[i * ldp + k1];
-            if (!zero) {
-                // the multiplier a[j] / pivot, held by the lane that owns column j
-                const double aj = __shfl_sync(0xffffffffu, j < 32 ? a0 : a1, j & 31);
-                const double l = aj / pv;
-                if (k0 > j && k0 < nw) a0 = fma(-l, prow[k0], a0);
-                if (k1 > j && k1 < nw) a1 = fma(-l, prow[k1], a1);
-                if (k0 == j) a0 = l;
-                if (k1 == j) a1 = l;
-            }
-            if (k0 < nw) P[i * ldp + k0] = a0;
-            if (k1 < nw) P[i * ldp + k1] = a1;
+            double a0 = 0.0, a1 = 0.0;
+            if (k0 < nw) a0 = lu_at<kInSmem>(S, P, ldp, r0, i, k0);
+            if (k1 < nw) a1 = lu_at<kInSmem>(S, P, ldp, r0, i, k1);
+            const double aj = __shfl_sync(0xffffffffu, j < 32 ? a0 : a1, j & 31);
+            const double l = aj / pv;
+            if (k0 > j && k0 < nw) a0 = fma(-l, prow[k0], a0);
+            if (k1 > j && k1 < nw) a1 = fma(-l, prow[k1], a1);
+            if (k0 == j) a0 = l;
+            if (k1 == j) a1 = l;
+            if (k0 < nw) lu_at<kInSmem>(S, P, ldp, r0, i, k0) = a0;
+            if (k1 < nw) lu_at<kInSmem>(S, P, ldp, r0, i, k1) = a1;
+        }
+    }
+    if constexpr (kInSmem) {
+        __syncthreads();
+        const int64_t n = (r1 > r0 ? r1 - r0 : 0) * nw;
+        for (int64_t e = tid; e < n; e += kLuThreads) {
+            const int64_t r = e / nw;
+            const int k = (int)(e % nw);
+            P[(r0 + r) * ldp + k] = S[r * kLuLd + k];
         }
     }
 }
@@ -331,11 +393,15 @@ struct Dev {
     int* err = nullptr;                  // error word of the tile kernels' bounded waits
     unsigned long long* info = nullptr;  // first failed Cholesky pivot (global column + 1)
     int64_t launches = 0;
-    // LU panel scratch: grid barrier words and per-CTA pivot candidates
+    // LU panel scratch: grid barrier words, per-CTA pivot candidates and their rows
+    // (two buffers each, by column parity), the published row j; lu_grid bounds the grid
     unsigned* bar = nullptr;
     double* cand_v = nullptr;
     int64_t* cand_i = nullptr;
+    double* cand_row = nullptr;
+    double* jrow = nullptr;
     int lu_grid = 0;
+    bool lu_rows_global = false;  // keep the panel's rows in global memory (the path for very tall panels)
     // Ozaki form for the in-HBM updates: digit-plane scratch (null: FP64 tiles)
     char* oz = nullptr;
     size_t oz_bytes = 0;
@@ -474,17 +540,41 @@ int launch_laswp(double* P, int64_t ldp, int64_t ncols, const int64_t* piv, int6
 int panel_lu(double* P, int64_t ldp, int64_t m, int64_t n, int64_t* piv, int64_t gofs, Dev& d, std::string& why)
 {
     if (n <= kSmall) {
-        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(d.lu_grid, (m + 31) / 32));
+        // rows in shared memory when a co-resident grid's slices fit, else in global memory
+        int64_t grid = std::max<int64_t>(1, std::min<int64_t>(d.lu_grid, (m + 31) / 32));
+        const int sms = device_sm_count();
+        bool in_smem = !d.lu_rows_global;
+        size_t smem = 0;
+        while (in_smem) {
+            smem = (size_t)((m + grid - 1) / grid) * kLuLd * sizeof(double);
+            int occ = 0;
+            if (smem > kLuSmemMax ||
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, narrow_lu_kernel<true>, kLuThreads, smem) !=
+                    cudaSuccess ||
+                occ == 0) {
+                cudaGetLastError();
+                in_smem = false;
+                break;
+            }
+            if ((int64_t)occ * sms >= grid) break;
+            grid = (int64_t)occ * sms;  // fewer, taller slices until the grid is co-resident
+        }
+        if (!in_smem) {
+            grid = std::max<int64_t>(1, std::min<int64_t>(d.lu_grid, (m + 31) / 32));
+            smem = 0;
+        }
         int64_t rows_per_cta = (m + grid - 1) / grid;
         unsigned* bar = d.bar;
         int nw = (int)n;
-        void* args[] = {&P, &ldp, &m, &nw, &rows_per_cta, &piv, &d.cand_v, &d.cand_i, &bar, &d.err, &d.info, &gofs};
+        void* args[] = {&P,         &ldp,    &m,    &nw,   &rows_per_cta, &piv,  &d.cand_v,
+                        &d.cand_i,  &d.cand_row, &d.jrow, &bar, &d.err, &d.info, &gofs};
         if (cudaMemsetAsync(d.bar, 0, 2 * sizeof(unsigned), d.st) != cudaSuccess) {
             why = "barrier reset failed";
             return OOC_ERR_CUDA;
         }
-        const cudaError_t e = cudaLaunchCooperativeKernel((const void*)narrow_lu_kernel, dim3((unsigned)grid),
-                                                          dim3(kLuThreads), args, 0, d.st);
+        const void* fn = in_smem ? (const void*)narrow_lu_kernel<true> : (const void*)narrow_lu_kernel<false>;
+        const cudaError_t e =
+            cudaLaunchCooperativeKernel(fn, dim3((unsigned)grid), dim3(kLuThreads), args, smem, d.st);
         ++d.launches;
         if (e != cudaSuccess) {
             cudaGetLastError();
@@ -888,10 +978,19 @@ int ooc_dgetrf(int64_t N, double* A, int64_t lda, int64_t* ipiv, size_t device_b
     if (!host_range_pinned(A, N, N, lda, 8))
         return fail(OOC_ERR_NOT_PINNED, "host operands must be page-locked (cudaHostAlloc / cudaHostRegister)");
     // panel width: the whole N x t panel, its pivots and the candidates in the arena
+    if (cudaFuncSetAttribute(narrow_lu_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLuSmemMax) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return fail(OOC_ERR_CUDA, "narrow_lu_kernel shared-memory attribute");
+    }
     int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, narrow_lu_kernel, kLuThreads, 0);
-    const int lu_grid = std::max(1, std::min(occ * device_sm_count(), 304));
-    const size_t fixed = 256 + 4096 + (size_t)lu_grid * 16 + 8 * 1024;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, narrow_lu_kernel<false>, kLuThreads, 0);
+    // panel kernel grid: co-resident, at most two CTAs per SM and one per 32 rows of the tallest panel
+    const int lu_grid =
+        (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)occ * device_sm_count(), 304, (N + 31) / 32}));
+    // its scratch: candidate values and rows (two buffers each), the published row j
+    const size_t lu_scratch = (size_t)lu_grid * 2 * (8 + 8 + kSmall * 8) + 2 * kSmall * 8;
+    const size_t fixed = 256 + 4096 + lu_scratch + 8 * 1024;
     auto panel_bytes = [&](int64_t w) { return (size_t)N * round_up64(w, 16) * 8; };
     const bool oz = opts && opts->form == OOC_FORM_OZAKI;
     auto oz_of = [&](int64_t w) { return oz ? ozaki_device_scratch(N, w, w) + 256 : (size_t)0; };
@@ -910,14 +1009,20 @@ int ooc_dgetrf(int64_t N, double* A, int64_t lda, int64_t* ipiv, size_t device_b
     double* dP = reinterpret_cast<double*>(dr.arena + 256);
     char* after = dr.arena + 256 + panel_bytes(t);
     int64_t* dpiv = reinterpret_cast<int64_t*>(after);
-    dr.d.cand_v = reinterpret_cast<double*>(after + 8 * 1024);
-    dr.d.cand_i = reinterpret_cast<int64_t*>(after + 8 * 1024 + (size_t)lu_grid * 8);
+    char* lu = after + 8 * 1024;
+    dr.d.cand_v = reinterpret_cast<double*>(lu);
+    dr.d.cand_i = reinterpret_cast<int64_t*>(lu + (size_t)lu_grid * 16);
+    dr.d.cand_row = reinterpret_cast<double*>(lu + (size_t)lu_grid * 32);
+    dr.d.jrow = reinterpret_cast<double*>(lu + (size_t)lu_grid * 32 + (size_t)lu_grid * 2 * kSmall * 8);
     dr.d.bar = reinterpret_cast<unsigned*>(dr.arena + 16);
     dr.d.lu_grid = lu_grid;
+    // OOC_LU_ROWS_GLOBAL=1: the panel kernel keeps its rows in global memory, the path taken
+    // when a co-resident grid's row slices do not fit shared memory (tests use it on small panels)
+    if (const char* g = std::getenv("OOC_LU_ROWS_GLOBAL")) dr.d.lu_rows_global = std::atoi(g) != 0;
     std::vector<int64_t> hpiv((size_t)t);
     // Ozaki updates: digit-plane scratch for the panel's largest in-HBM update (rows N, order t),
     // then the U12 row panel in column chunks
-    size_t used = (256 + panel_bytes(t) + 8 * 1024 + (size_t)lu_grid * 16 + 255) / 256 * 256;
+    size_t used = (256 + panel_bytes(t) + 8 * 1024 + lu_scratch + 255) / 256 * 256;
     if (oz_bytes) {
         dr.d.oz = dr.arena + used;
         dr.d.oz_bytes = oz_bytes;

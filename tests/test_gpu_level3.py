@@ -359,6 +359,22 @@ def test_dgetrf_zero_pivot_sets_info(ooc, zero_col):
     assert oracle.rel_fro(np64(A), F) <= 1e-12
 
 
+@pytest.mark.parametrize("n,budget,zero_col", [(500, 512 << 10, None), (1100, 64 << 20, None), (300, 256 << 10, 70)])
+def test_dgetrf_panel_rows_in_global_memory(ooc, n, budget, zero_col, monkeypatch):
+    """The panel kernel's other path (rows kept in global memory, taken when a co-resident
+    grid's row slices do not fit shared memory), forced here on panels that would fit."""
+    monkeypatch.setenv("OOC_LU_ROWS_GLOBAL", "1")
+    A = pinned_from(180 + n, 0, n, n, synth.NORMAL)
+    if zero_col is not None:
+        A.numpy()[:, zero_col] = 0.0
+    A0 = np64(A)
+    ipiv, info, _ = _getrf(ooc, A, budget)
+    F, rpiv, rinfo = level3.getrf(A0)
+    assert info == rinfo == (0 if zero_col is None else zero_col + 1)
+    assert list(ipiv) == list(rpiv)
+    assert oracle.rel_fro(np64(A), F) <= 1e-12
+
+
 def test_dgetrf_bad_arguments(ooc):
     A = pinned(8, 8)
     ipiv = np.zeros(8, dtype=np.int64)
