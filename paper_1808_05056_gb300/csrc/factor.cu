@@ -22,6 +22,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <string>
 #include <thread>
 #include <vector>
@@ -1032,8 +1033,9 @@ int ooc_dgetrf(int64_t N, double* A, int64_t lda, int64_t* ipiv, size_t device_b
     double* dU = reinterpret_cast<double*>(dr.arena + used);
     const int64_t u_chunk = std::max<int64_t>(16, (int64_t)(u_bytes / (8 * (size_t)round_up64(t, 16)) / 16 * 16) - 16);
     // OOC_TRACE=<file>: one line per panel with the host time of each phase (ms)
-    FILE* trace = nullptr;
-    if (const char* tp = std::getenv("OOC_TRACE")) trace = std::fopen(tp, "a");
+    std::unique_ptr<FILE, int (*)(FILE*)> trace_file(nullptr, std::fclose);
+    if (const char* tp = std::getenv("OOC_TRACE")) trace_file.reset(std::fopen(tp, "a"));
+    FILE* trace = trace_file.get();
     if (trace) std::fprintf(trace, "# getrf N=%lld t=%lld: c0,panel,laswp,u12,gemm\n", (long long)N, (long long)t);
     auto now = [] { return std::chrono::steady_clock::now(); };
     auto ms = [](std::chrono::steady_clock::time_point a, std::chrono::steady_clock::time_point b) {
@@ -1078,7 +1080,7 @@ int ooc_dgetrf(int64_t N, double* A, int64_t lda, int64_t* ipiv, size_t device_b
             std::fprintf(trace, "%lld,%.2f,%.2f,%.2f,%.2f\n", (long long)c0, ms(p0, p1), ms(p1, p2), ms(p2, p3),
                          ms(p3, p4));
     }
-    if (trace) std::fclose(trace);
+    trace_file.reset();
     unsigned long long hinfo = 0;
     if (cudaMemcpy(&hinfo, dr.d.info, sizeof(hinfo), cudaMemcpyDeviceToHost) != cudaSuccess)
         return fail(OOC_ERR_CUDA, "pivot word read failed");
