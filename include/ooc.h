@@ -268,7 +268,9 @@ int ooc_dpotrf(char uplo, int64_t N, double* A, int64_t lda, size_t device_budge
  * place, A = P L U: L unit lower triangular (stored below the diagonal), U
  * upper triangular (on and above it).  ipiv (host, N entries, 0-based): at
  * step j row j was exchanged with row ipiv[j] >= j, applied in order j = 0, 1,
- * ...; the pivot is the first row with the largest |a| in the column.  Right-
+ * ...; the pivot is the first row with the largest |a| in the column (a NaN
+ * is never chosen while a number remains; a column with no comparable entry
+ * keeps row j).  Right-
  * looking over panels of t columns: the (N - c0) x t panel is factored in
  * device memory (recursive halving; 64-column panels by one cooperative kernel
  * with a bounded grid barrier per pivot), its interchanges are applied to the
