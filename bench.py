@@ -100,7 +100,60 @@ def parse():
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--form", default="", choices=["", "fp64", "ozaki"],
                     help="GEMM form of the level-3 configurations' updates (default FP64)")
+    ap.add_argument("--repeat-ci", type=float, default=0.0, metavar="F",
+                    help="GEMM configurations, one process: Section V's rule instead of exactly --steps timed "
+                         "steps: at least max(3, steps), then more until the Student-t 95%% confidence "
+                         "half-width of the step time is within F of its mean (the paper: 0.025)")
+    ap.add_argument("--repeat-max-s", type=float, default=600.0,
+                    help="cap on the timed seconds under --repeat-ci")
     return ap.parse_args()
+
+
+# two-sided 95 % Student-t quantiles t(0.975, df); between entries the smaller df's (larger) value
+T975 = ((1, 12.706), (2, 4.303), (3, 3.182), (4, 2.776), (5, 2.571), (6, 2.447), (7, 2.365), (8, 2.306),
+        (9, 2.262), (10, 2.228), (12, 2.179), (15, 2.131), (20, 2.086), (25, 2.060), (30, 2.042),
+        (40, 2.021), (60, 2.000), (120, 1.980))
+
+
+def t975(df):
+    try:
+        from scipy import stats
+        return float(stats.t.ppf(0.975, df))
+    except ImportError:
+        return [t for d, t in T975 if d <= df][-1]
+
+
+def ci95(xs):
+    """Mean and Student-t 95 % confidence half-width of independent observations (Section V)."""
+    n = len(xs)
+    if n < 2:
+        return None
+    mean = statistics.fmean(xs)
+    hw = t975(n - 1) * statistics.stdev(xs) / n ** 0.5
+    return {"n": n, "mean_s": mean, "half_width_s": hw, "frac": hw / mean if mean > 0 else None}
+
+
+def run_timed(step, args, seconds_of, world):
+    """The timed steps: exactly --steps, or with --repeat-ci F Section V's rule -- at least
+    max(3, --steps), then one more at a time until the 95 % confidence half-width of the step
+    time is within F of its mean or the timed steps reach --repeat-max-s seconds."""
+    out = [step() for _ in range(args.steps)]
+    if args.repeat_ci <= 0:
+        return out, None
+    if world > 1:
+        raise SystemExit("--repeat-ci runs one process (the stopping rule is per process)")
+    while len(out) < 3:
+        out.append(step())
+    while True:
+        c = ci95([seconds_of(o) for o in out])
+        spent = sum(seconds_of(o) for o in out)
+        if c["frac"] is not None and c["frac"] <= args.repeat_ci or spent >= args.repeat_max_s:
+            break
+        out.append(step())
+    c["rule"] = "Section V: repeat until the Student-t 95%% half-width <= %.3f of the mean (min 3, cap %.0f s)" % (
+        args.repeat_ci, args.repeat_max_s)
+    c["met"] = c["frac"] is not None and c["frac"] <= args.repeat_ci
+    return out, c
 
 
 def workload(args):
@@ -345,13 +398,12 @@ def run_ours(args, w, world, rank, local, pg):
     if pg:
         pg.barrier()
     torch.cuda.synchronize()
-    stats = []
-    for _ in range(args.steps):
-        stats.append(step())
+    stats, repeat = run_timed(step, args, lambda o: o[0].device_seconds, world)
     torch.cuda.synchronize()
     if pg:
         pg.barrier()
     clocks = clk.stop()
+    n_steps = len(stats)
 
     dev_s = sum(s.device_seconds for s, _ in stats)
     wall_s = sum(wl for _, wl in stats)
@@ -361,8 +413,8 @@ def run_ours(args, w, world, rank, local, pg):
     if rank != 0:
         return
     flops = 2.0 * M * N * K
-    value = world * flops * args.steps / dev_s / 1e12
-    e2e = world * flops * args.steps / wall_s / 1e12
+    value = world * flops * n_steps / dev_s / 1e12
+    e2e = world * flops * n_steps / wall_s / 1e12
     pk, pk_src = peaks()
     s0 = stats[0][0]
     link_h2d, link_d2h = P.ooc_query_device()[1:]
@@ -371,7 +423,7 @@ def run_ours(args, w, world, rank, local, pg):
     traffic = tr["bytes"] if tr and not args.n and (s0.mb, s0.nb, s0.kb) == tr["plan"] else None
     if w["form"] == "fp64":
         peak = pk["bf16_tflops_sustained"] * NOMINAL_FP64_TF / NOMINAL_BF16_TF
-        achieved = flops * args.steps / ker_s / 1e12
+        achieved = flops * n_steps / ker_s / 1e12
         roof = {"bound": "tensor", "kernel": "fp64_tile_kernel (FP64 mma.sync, TMA-fed)",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                 "traffic_alg_bytes": 8.0 * (s0.mb * s0.kb + s0.kb * s0.nb + 2 * s0.mb * s0.nb),
@@ -383,7 +435,7 @@ def run_ours(args, w, world, rank, local, pg):
         compute_peak = peak
     else:
         peak = pk["bf16_tflops_sustained"]
-        achieved = flops * s0.products * args.steps / ker_s / 1e12
+        achieved = flops * s0.products * n_steps / ker_s / 1e12
         roof = {"bound": "tensor",
                 "kernel": "tc_terms_kernel (tcgen05 bf16 x bf16 -> f32 TMEM, TMA) with its split kernels",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
@@ -392,19 +444,19 @@ def run_ours(args, w, world, rank, local, pg):
                 "traffic_source": tr["profile"] if traffic else None,
                 "flop_count": "2*M*N*K x %d bf16 products per logical product" % s0.products,
                 "peak_source": "%s bf16 sustained (cuBLAS) %.1f TF" % (pk_src, peak),
-                "logical_tflops": flops * args.steps / ker_s / 1e12, "launches_per_step": s0.steps}
+                "logical_tflops": flops * n_steps / ker_s / 1e12, "launches_per_step": s0.steps}
         compute_peak = peak / s0.products
     t_roof = max(flops / (compute_peak * 1e12), s0.h2d_bytes / (link_h2d * 1e9), s0.d2h_bytes / (link_d2h * 1e9))
     host_gib = (M * K + K * N + M * N) * (4 if w["form"] == "bf16x3" else 8) / 2 ** 30
     line = {
         "metric": "out-of-core GEMM effective TFLOP/s incl. transfers",
-        "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * dev_s / args.steps, "higher_is_better": True, "scaling": "weak",
+        "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": n_steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dev_s / n_steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": dtag, "data": "synthetic (seeded Philox, pinned host)",
         "config": config_json(w, "inputs larger than L2: %.0f GiB host operands streamed through a %.2f GiB "
                                  "device budget each step" % (host_gib, w["budget"] / 2 ** 30)),
         "roofline": roof,
-        "ooc_roofline": {"t_roof_s": t_roof, "t_step_s": dev_s / args.steps, "frac": t_roof / (dev_s / args.steps),
+        "ooc_roofline": {"t_roof_s": t_roof, "t_step_s": dev_s / n_steps, "frac": t_roof / (dev_s / n_steps),
                          "compute_peak_logical_tflops": compute_peak, "h2d_gbps": link_h2d, "d2h_gbps": link_d2h,
                          "h2d_bytes": s0.h2d_bytes, "d2h_bytes": s0.d2h_bytes, "bytes_alg": b_alg},
         "plan": {"mb": s0.mb, "nb": s0.nb, "kb": s0.kb, "depth": s0.depth, "b_buffers": s0.b_buffers,
@@ -417,6 +469,7 @@ def run_ours(args, w, world, rank, local, pg):
         "cpu_baseline": cpu,
         "clocks": clocks,
         "setup_fill_s": t_fill,
+        "repeat": repeat if repeat else ci95([st.device_seconds for st, _ in stats]),
     }
     print(json.dumps(line), flush=True)
 
@@ -524,11 +577,12 @@ def run_batched_bench(args, w, world, rank, local, pg):
     if pg:
         pg.barrier()
     torch.cuda.synchronize()
-    stats = [step() for _ in range(args.steps)]
+    stats, repeat = run_timed(step, args, lambda o: o[0].device_seconds, world)
     torch.cuda.synchronize()
     if pg:
         pg.barrier()
     clocks = clk.stop()
+    n_steps = len(stats)
     dev_s = sum(st.device_seconds for st, _ in stats)
     wall_s = sum(wl for _, wl in stats)
     ker_s = sum(st.kernel_seconds for st, _ in stats)
@@ -539,11 +593,11 @@ def run_batched_bench(args, w, world, rank, local, pg):
     pk, pk_src = peaks()
     peak = pk["bf16_tflops_sustained"] * NOMINAL_FP64_TF / NOMINAL_BF16_TF
     # the two halves' kernels overlap, so the summed kernel time over-counts: device time instead
-    achieved = flops * args.steps / dev_s / 1e12 if dev_s > 0 else None
+    achieved = flops * n_steps / dev_s / 1e12 if dev_s > 0 else None
     line = {
         "metric": "out-of-core GEMM effective TFLOP/s incl. transfers",
-        "value": world * flops * args.steps / dev_s / 1e12, "unit": "TFLOP/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dev_s / args.steps,
+        "value": world * flops * n_steps / dev_s / 1e12, "unit": "TFLOP/s", "n_gpus": world,
+        "steps": n_steps, "warmup": args.warmup, "ms_per_step": 1e3 * dev_s / n_steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded Philox N(0,1), pinned host)",
         "config": {"workload": "%d uneven FP64 GEMMs, M,N,K log-uniform in [%d, %d] (seed 1234), %.1f GiB host, "
@@ -557,10 +611,11 @@ def run_batched_bench(args, w, world, rank, local, pg):
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak if achieved else None, "traffic": None,
                      "peak_source": "%s bf16 sustained x nominal FP64/BF16 ratio" % pk_src},
-        "e2e": {"value": world * flops * args.steps / wall_s / 1e12, "unit": "TFLOP/s",
+        "e2e": {"value": world * flops * n_steps / wall_s / 1e12, "unit": "TFLOP/s",
                 "h2d_bytes_per_step": s0.h2d_bytes, "d2h_bytes_per_step": s0.d2h_bytes},
         "gpu_launches": sum(st.kernel_launches for st, _ in stats),
         "parity": parity, "cpu_baseline": cpu, "clocks": clocks, "setup_fill_s": t_fill,
+        "repeat": repeat if repeat else ci95([st.device_seconds for st, _ in stats]),
     }
     print(json.dumps(line), flush=True)
 
