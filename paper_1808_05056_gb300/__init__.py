@@ -184,8 +184,16 @@ def _ptr(x):
 
 
 def _ld(x):
+    """Leading dimension (elements between rows) of a row-major 2-D tensor / array whose rows
+    are contiguous; raises ValueError for views with strided rows (the C ABI cannot express them)."""
     if hasattr(x, "stride"):
+        if x.dim() == 2 and x.shape[1] > 1 and x.stride(1) != 1:
+            raise ValueError("rows must be contiguous (stride 1 along the last dimension), got strides %s"
+                             % (tuple(x.stride()),))
         return x.stride(0) if x.dim() == 2 and x.shape[0] > 1 else max(1, x.shape[-1])
+    if x.ndim == 2 and x.shape[1] > 1 and x.strides[1] != x.itemsize:
+        raise ValueError("rows must be contiguous (stride 1 along the last dimension), got strides %s"
+                         % (tuple(x.strides),))
     return x.strides[0] // x.itemsize if x.shape[0] > 1 else max(1, x.shape[-1])
 
 

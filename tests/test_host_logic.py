@@ -53,6 +53,26 @@ def test_invalid_arguments_rejected_before_device():
     assert P.ooc_dgemm("N", "N", 0, 5, 5, 1.0, None, 5, None, 5, 0.0, None, 5, 1 << 20) == P.OOC_OK
 
 
+def test_leading_dimension_of_row_major_views():
+    """The binding passes views whose rows are contiguous (padding between rows is fine) and
+    rejects views with strided rows, which the C ABI's (pointer, ld) pair cannot describe."""
+    import numpy as np
+    import torch
+    t = torch.zeros(8, 16, dtype=torch.float64)
+    assert P._ld(t) == 16
+    assert P._ld(t[:, :10]) == 16          # padded rows: ld 16 for 10 columns
+    assert P._ld(t[:, 3:4]) == 16          # one column: no stride within a row
+    assert P._ld(t[2:3, :]) == 16          # one row
+    for bad in (t[:, ::2], t.t()):
+        with pytest.raises(ValueError):
+            P._ld(bad)
+    a = np.zeros((8, 16))
+    assert P._ld(a) == 16 and P._ld(a[:, :10]) == 16
+    for bad in (a[:, ::2], a.T):
+        with pytest.raises(ValueError):
+            P._ld(bad)
+
+
 def test_paper_mode_worked_example():
     plan = P.ooc_plan(4, 4, 8, 8, 1, 44 * 8, P.make_opts(flags=P.OOC_PLAN_PAPER))
     assert plan["blocks"] == 8 and (plan["mb"], plan["nb"], plan["kb"]) == (1, 2, 8)
