@@ -380,7 +380,8 @@ def ooc_dgemm_batched(descs, budget, opts=None, stats=None):
 
 
 def gemm_desc(transA, transB, A, B, C, alpha=1.0, beta=0.0):
-    """An ooc_gemm_desc for pinned host tensors (shapes as in dgemm)."""
+    """An ooc_gemm_desc for pinned host tensors (shapes as in dgemm): float64 for
+    ooc_dgemm_batched, float64 or float32 for ooc_autotune (whose elem_bytes says which)."""
     M, N, K = _shape_args(transA, transB, A, B, C)
     d = ooc_gemm_desc()
     d.transA, d.transB = transA.encode(), transB.encode()
@@ -577,17 +578,40 @@ def ooc_last_error():
 
 
 # ------------------------------------------------------------------ helpers --
-def _shape_args(transA, transB, A, B, C):
+def _shape_args(transA, transB, A, B, C, itemsize=(4, 8)):
+    """M, N, K of C = op(A) op(B) for 2-D operands; ValueError when the shapes do not chain, or the
+    three operands are not floating point of one element size allowed by the call (8 for dgemm,
+    4 for sgemm, either for a batched / autotune descriptor)."""
+    allowed = (itemsize,) if isinstance(itemsize, int) else tuple(itemsize)
+    sizes = set()
+    for name, x in (("A", A), ("B", B), ("C", C)):
+        if len(x.shape) != 2:
+            raise ValueError("%s must be 2-D, got shape %s" % (name, tuple(x.shape)))
+        es = x.element_size() if hasattr(x, "element_size") else x.itemsize
+        if es not in allowed or not _is_float(x):
+            raise ValueError("%s must hold floating-point elements of %s bytes, got %s" % (
+                name, " or ".join(map(str, allowed)), x.dtype))
+        sizes.add(es)
+    if len(sizes) != 1:
+        raise ValueError("A, B and C must have one element type")
     M = A.shape[0] if transA in "Nn" else A.shape[1]
     K = A.shape[1] if transA in "Nn" else A.shape[0]
     N = B.shape[1] if transB in "Nn" else B.shape[0]
-    assert tuple(C.shape) == (M, N)
+    KB = B.shape[0] if transB in "Nn" else B.shape[1]
+    if KB != K or tuple(C.shape) != (M, N):
+        raise ValueError("shapes do not chain: op(A) %dx%d, op(B) %dx%d, C %s" % (M, K, KB, N, tuple(C.shape)))
     return M, N, K
+
+
+def _is_float(x):
+    if hasattr(x, "is_floating_point"):
+        return x.is_floating_point() and not x.is_complex()
+    return x.dtype.kind == "f"
 
 
 def dgemm(A, B, C, alpha=1.0, beta=0.0, budget=4 << 30, transA="N", transB="N", opts=None):
     """In place C = alpha*op(A)*op(B) + beta*C on pinned float64 host tensors; returns stats dict."""
-    M, N, K = _shape_args(transA, transB, A, B, C)
+    M, N, K = _shape_args(transA, transB, A, B, C, 8)
     st = ooc_stats()
     _check(ooc_dgemm(transA, transB, M, N, K, alpha, A, _ld(A), B, _ld(B), beta, C, _ld(C), budget,
                      opts, st), "ooc_dgemm")
@@ -596,7 +620,7 @@ def dgemm(A, B, C, alpha=1.0, beta=0.0, budget=4 << 30, transA="N", transB="N", 
 
 def sgemm(A, B, C, alpha=1.0, beta=0.0, budget=4 << 30, transA="N", transB="N", opts=None):
     """In place FP32 C = alpha*op(A)*op(B) + beta*C (BF16x3 form) on pinned float32 host tensors."""
-    M, N, K = _shape_args(transA, transB, A, B, C)
+    M, N, K = _shape_args(transA, transB, A, B, C, 4)
     st = ooc_stats()
     _check(ooc_sgemm(transA, transB, M, N, K, alpha, A, _ld(A), B, _ld(B), beta, C, _ld(C), budget,
                      opts, st), "ooc_sgemm")

@@ -73,6 +73,28 @@ def test_leading_dimension_of_row_major_views():
             P._ld(bad)
 
 
+def test_gemm_helpers_check_shapes_and_types():
+    import torch
+    f8 = lambda r, c: torch.zeros(r, c, dtype=torch.float64)
+    f4 = lambda r, c: torch.zeros(r, c, dtype=torch.float32)
+    assert P._shape_args("N", "N", f8(5, 3), f8(3, 4), f8(5, 4), 8) == (5, 4, 3)
+    assert P._shape_args("T", "T", f8(3, 5), f8(4, 3), f8(5, 4), 8) == (5, 4, 3)
+    assert P._shape_args("N", "N", f4(5, 3), f4(3, 4), f4(5, 4)) == (5, 4, 3)
+    bad = [
+        (("N", "N", f8(5, 3), f8(2, 4), f8(5, 4), 8), "chain"),        # inner dimensions differ
+        (("N", "T", f8(5, 3), f8(3, 4), f8(5, 4), 8), "chain"),        # op(B) is 4 x 3
+        (("N", "N", f8(5, 3), f8(3, 4), f8(4, 5), 8), "chain"),        # C the wrong shape
+        (("N", "N", f4(5, 3), f4(3, 4), f4(5, 4), 8), "bytes"),        # float32 into dgemm
+        (("N", "N", f8(5, 3), f8(3, 4), f8(5, 4), 4), "bytes"),        # float64 into sgemm
+        (("N", "N", f8(5, 3), f4(3, 4), f8(5, 4)), "one element type"),
+        (("N", "N", torch.zeros(5, 3, dtype=torch.int64), f8(3, 4), f8(5, 4), 8), "bytes"),
+        (("N", "N", f8(5, 3)[0], f8(3, 4), f8(5, 4), 8), "2-D"),
+    ]
+    for args, msg in bad:
+        with pytest.raises(ValueError, match=msg):
+            P._shape_args(*args)
+
+
 def test_paper_mode_worked_example():
     plan = P.ooc_plan(4, 4, 8, 8, 1, 44 * 8, P.make_opts(flags=P.OOC_PLAN_PAPER))
     assert plan["blocks"] == 8 and (plan["mb"], plan["nb"], plan["kb"]) == (1, 2, 8)
