@@ -53,6 +53,42 @@ def test_invalid_arguments_rejected_before_device():
     assert P.ooc_dgemm("N", "N", 0, 5, 5, 1.0, None, 5, None, 5, 0.0, None, 5, 1 << 20) == P.OOC_OK
 
 
+def test_missing_library_fails_loudly(tmp_path):
+    with pytest.raises(RuntimeError, match="not built"):
+        P.load(str(tmp_path / "libooc.so"))
+
+
+@pytest.mark.skipif(__import__("torch").cuda.is_available(), reason="needs a machine without a GPU")
+def test_no_cpu_fallback_without_a_device():
+    """Every compute entry point returns an error on a machine with no sm_103 device and leaves
+    the host data untouched: there is no CPU path behind the C ABI."""
+    import numpy as np
+    A, B = np.ones((4, 4)), np.ones((4, 4))
+    C = np.full((4, 4), 7.0)
+    A4, C4 = np.ones((4, 4), dtype=np.float32), np.full((4, 4), 7.0, dtype=np.float32)
+    ipiv = np.zeros(4, dtype=np.int64)
+    nd = P.OOC_ERR_NO_DEVICE
+    assert P.ooc_dgemm("N", "N", 4, 4, 4, 1.0, A, 4, B, 4, 0.0, C, 4, 1 << 20) == nd
+    assert P.ooc_sgemm("N", "N", 4, 4, 4, 1.0, A4, 4, A4, 4, 0.0, C4, 4, 1 << 20) == nd
+    assert P.ooc_dgemmt("L", "N", "N", 4, 4, 1.0, A, 4, B, 4, 0.0, C, 4, 1 << 20) == nd
+    assert P.ooc_dsyrk("L", "N", 4, 4, 1.0, A, 4, 0.0, C, 4, 1 << 20) == nd
+    assert P.ooc_ssyrk("L", "N", 4, 4, 1.0, A4, 4, 0.0, C4, 4, 1 << 20) == nd
+    assert P.ooc_dtrsm("L", "L", "N", "N", 4, 4, 1.0, A, 4, C, 4, 1 << 20) == nd
+    assert P.ooc_dpotrf("L", 4, C, 4, 1 << 20)[0] == nd
+    assert P.ooc_dgetrf(4, C, 4, ipiv, 1 << 20)[0] == nd
+    assert P.ooc_dgemm_batched([P.gemm_desc("N", "N", A, B, C)], 1 << 20) == nd
+    assert P.ooc_dgemm_device("N", "N", 4, 4, 4, 1.0, 1, 4, 1, 4, 0.0, 1, 4) == nd
+    assert P.ooc_dgemm_noalloc("N", "N", 4, 4, 4, 1.0, A, 4, B, 4, 0.0, C, 4, 1 << 20) in (nd, P.OOC_ERR_NOT_PINNED)
+    assert P.Session(4, 4, C, 4, 0.0, 1 << 20).rc == nd
+    pipe = P.Pipe(P.MMOOC_PIPELINE)
+    for name, v in dict(mb=4, nb=4, kb=4, ra=2, rb=2, rc=2, alpha=1.0, beta=0.0, beta_nz=0).items():
+        pipe.set(name, v)
+    for name, t in (("A", A), ("B", B), ("C", C)):
+        pipe.bind(name, t)
+    assert pipe.run(1 << 20) == nd
+    assert (C == 7.0).all() and (C4 == 7.0).all() and (ipiv == 0).all()
+
+
 def test_leading_dimension_of_row_major_views():
     """The binding passes views whose rows are contiguous (padding between rows is fine) and
     rejects views with strided rows, which the C ABI's (pointer, ld) pair cannot describe."""
