@@ -167,8 +167,12 @@ int ooc_dgemm_batched(int32_t count, const ooc_gemm_desc* descs, size_t device_b
  * compute stage): C = alpha * op(A) * op(B) + beta * C on device pointers,
  * FP64, enqueued on `stream` (a cudaStream_t, NULL = legacy default stream)
  * and not synchronised.  Same layout rules as ooc_dgemm, plus 16-byte aligned
- * device bases and even leading dimensions (else OOC_ERR_UNSUPPORTED); the
- * first call allocates a 4-byte device error word kept for the process.
+ * device bases and even leading dimensions (else OOC_ERR_UNSUPPORTED).  The
+ * first call on each device allocates a 4-byte device error word kept for the
+ * process; every call clears it on `stream` before its launch.  The call does
+ * not wait for the kernel, so it cannot report a device-side wait that gave up
+ * (the kernel's bounded waits end it early in that case and C is left
+ * incomplete); callers that need that status use ooc_dgemm.
  */
 int ooc_dgemm_device(char transA, char transB, int64_t M, int64_t N, int64_t K, double alpha,
                      const double* dA, int64_t lda, const double* dB, int64_t ldb, double beta,
@@ -189,7 +193,8 @@ int ooc_dgemm_device(char transA, char transB, int64_t M, int64_t N, int64_t K, 
  * operands) with device_budget_bytes <= OOC_NOALLOC_MAX_BYTES, else
  * OOC_ERR_INVALID_ARG.  The call is synchronous.  The first call on a device
  * (that device current) looks up the array's address; make it before any
- * stream capture.  All calls share the array and it keeps the last call's
+ * stream capture.  The address is kept for the process: do not call this
+ * entry point again after cudaDeviceReset.  All calls share the array and it keeps the last call's
  * contents; calls that overlap on the GPU race, so serialise them.
  */
 #define OOC_NOALLOC_MAX_BYTES (32u << 20)

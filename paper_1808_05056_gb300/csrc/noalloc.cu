@@ -16,7 +16,9 @@
 //
 // Set-up: the first call on a device (with that device current) looks up the
 // array's device address with cudaGetSymbolAddress and caches it; make that
-// first call before any stream capture begins.  All calls share the array and
+// first call before any stream capture begins.  The cached address belongs to
+// the device's primary context: after cudaDeviceReset (or any other reset of
+// that context) the library must not be called again in the process.  All calls share the array and
 // it keeps the last call's contents: the call clears the error word it needs
 // at zero, and the plan never reads a slot before writing it.  Calls that
 // overlap on the GPU (on different streams, or from several host threads)
@@ -107,13 +109,15 @@ extern "C" int ooc_dgemm_noalloc(char transA, char transB, int64_t M, int64_t N,
                                 " bytes");
     if (M == 0 || N == 0) return OOC_OK;
     if ((K > 0 && (!A || !B)) || !C) return noalloc_fail(OOC_ERR_INVALID_ARG, "null operand pointer");
+    std::string why;
+    int rc = device_check(why);
+    if (rc) return noalloc_fail(rc, why);
     if (!pinned_range(A, ta ? K : M, ta ? M : K, lda) || !pinned_range(B, tb ? N : K, tb ? K : N, ldb) ||
         !pinned_range(C, M, N, ldc))
         return noalloc_fail(OOC_ERR_NOT_PINNED, "host operands must be page-locked");
 
-    std::string why;
     char* arena = nullptr;
-    int rc = arena_for_current_device(&arena, why);
+    rc = arena_for_current_device(&arena, why);
     if (rc) return noalloc_fail(rc, why);
 
     ooc_opts opts;
@@ -190,10 +194,14 @@ extern "C" int ooc_dgemm_noalloc(char transA, char transB, int64_t M, int64_t N,
             return noalloc_fail(OOC_ERR_CUDA, std::string("ooc_dgemm_noalloc copy: ") + cudaGetErrorString(e));
         }
     }
-    if (cudaStreamSynchronize(st) != cudaSuccess) return noalloc_fail(OOC_ERR_CUDA, "stream synchronize");
+    // the error word is read on the caller's stream, behind the last kernel,
+    // into pageable host memory (the copy completes before the synchronize returns)
     int herr = 0;
-    if (cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    if (cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) {
+        cudaStreamSynchronize(st);
         return noalloc_fail(OOC_ERR_CUDA, "reading the error word");
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess) return noalloc_fail(OOC_ERR_CUDA, "stream synchronize");
     if (herr) return noalloc_fail(OOC_ERR_TIMEOUT, "a device-side wait gave up");
     return OOC_OK;
 }

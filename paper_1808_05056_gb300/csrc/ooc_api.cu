@@ -310,9 +310,11 @@ bool range_pinned(const void* base, int64_t rows, int64_t cols, int64_t ld, int 
     return pinned(b) && pinned(last);
 }
 
-// OOC_FAULT_INJECT=alloc | copy:<n> | kernel:<n>  (host-side failures for tests)
+// OOC_FAULT_INJECT=alloc | copy:<n> | kernel:<n> | devword  (host-side failures
+// for tests; devword: ooc_dgemm_device leaves its error word nonzero after its
+// launch, as a wait that gave up would)
 struct Inject {
-    bool alloc = false;
+    bool alloc = false, devword = false;
     long copy = -1, kernel = -1;
     Inject()
     {
@@ -320,6 +322,7 @@ struct Inject {
         if (!e) return;
         std::string s(e);
         if (s == "alloc") alloc = true;
+        else if (s == "devword") devword = true;
         else if (s.rfind("copy:", 0) == 0) copy = std::atol(s.c_str() + 5);
         else if (s.rfind("kernel:", 0) == 0) kernel = std::atol(s.c_str() + 7);
     }
@@ -1300,16 +1303,36 @@ int ooc_dgemm_device(char transA, char transB, int64_t M, int64_t N, int64_t K, 
     if ((lda % 2) || (ldb % 2) || (ldc % 2) || (reinterpret_cast<uintptr_t>(dA) % 16) ||
         (reinterpret_cast<uintptr_t>(dB) % 16) || (reinterpret_cast<uintptr_t>(dC) % 16))
         return fail(OOC_ERR_UNSUPPORTED, "device operands need 16-byte aligned bases and even leading dimensions");
-    static int* err = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        if (cudaMalloc(&err, sizeof(int)) == cudaSuccess) cudaMemset(err, 0, sizeof(int));
-        else err = nullptr;
-    });
-    if (!err) return fail(OOC_ERR_ALLOC, "error word");
+    // one error word per device, allocated by the first call on that device
+    // and cleared on the caller's stream before every launch, so that a wait
+    // that gave up in an earlier call cannot end this call's kernel early
+    constexpr int kMaxDev = 64;
+    static std::mutex mu;
+    static int* words[kMaxDev] = {nullptr};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
+        cudaGetLastError();
+        return fail(OOC_ERR_NO_DEVICE, "no current CUDA device");
+    }
+    int* err = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!words[dev]) {
+            if (cudaMalloc(&words[dev], sizeof(int)) != cudaSuccess) {
+                cudaGetLastError();
+                words[dev] = nullptr;
+                return fail(OOC_ERR_ALLOC, "error word");
+            }
+        }
+        err = words[dev];
+    }
+    if (cudaMemsetAsync(err, 0, sizeof(int), static_cast<cudaStream_t>(stream)) != cudaSuccess)
+        return fail(OOC_ERR_CUDA, "clearing the error word");
     rc = launch_fp64_tile(is_n(transA), is_t(transB), M, N, K, alpha, dA, lda, dB, ldb, beta, beta != 0.0, dC, ldc,
                           err, stream, why);
     if (rc) return fail(rc, why);
+    if (Inject().devword && cudaMemsetAsync(err, 0x7F, sizeof(int), static_cast<cudaStream_t>(stream)) != cudaSuccess)
+        return fail(OOC_ERR_CUDA, "injected error word");
     return OOC_OK;
 }
 

@@ -185,3 +185,29 @@ def test_device_entry_in_core(ooc, ta, tb):
     torch.cuda.synchronize()
     ref = oracle.gemm(ta, tb, 0.75, A, B, -1.25, C)
     assert oracle.rel_fro(dC[:, :N].cpu().numpy(), ref) <= TOL
+
+
+def test_device_entry_clears_error_word_between_calls(ooc, monkeypatch):
+    """ooc_dgemm_device keeps one error word per device and clears it on the caller's stream
+    before each launch: a word left nonzero by an earlier call (injected on the host after the
+    first call's kernel, as a wait that gave up would leave it) must not cut the next call's
+    kernel short.  K spans many stages so the producer's waits take their slow path, which is
+    where the word is read."""
+    M, N, K = 512, 384, 4096
+    A = synth.matrix(M, K, 11, 0, synth.NORMAL)
+    B = synth.matrix(K, N, 11, 1, synth.NORMAL)
+    dA = torch.from_numpy(A).cuda()
+    dB = torch.from_numpy(B).cuda()
+    ref = oracle.gemm("N", "N", 1.0, A, B, 0.0, np.zeros((M, N)))
+    monkeypatch.setenv("OOC_FAULT_INJECT", "devword")
+    for _ in range(2):
+        dC = torch.full((M, N), np.nan, dtype=torch.float64, device="cuda")
+        rc = ooc.ooc_dgemm_device("N", "N", M, N, K, 1.0, dA, K, dB, N, 0.0, dC, N, None)
+        assert rc == 0, ooc.ooc_last_error()
+        torch.cuda.synchronize()
+        assert oracle.rel_fro(dC.cpu().numpy(), ref) <= TOL
+    monkeypatch.delenv("OOC_FAULT_INJECT")
+    dC = torch.full((M, N), np.nan, dtype=torch.float64, device="cuda")
+    assert ooc.ooc_dgemm_device("N", "N", M, N, K, 1.0, dA, K, dB, N, 0.0, dC, N, None) == 0
+    torch.cuda.synchronize()
+    assert oracle.rel_fro(dC.cpu().numpy(), ref) <= TOL

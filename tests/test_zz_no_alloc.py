@@ -18,7 +18,7 @@ pytestmark = pytest.mark.gpu
 TOL = 1e-13
 
 
-def _pair(ooc, seed, ta, tb, M, N, K, alpha, beta, budget):
+def _pair(ooc, seed, ta, tb, M, N, K, alpha, beta, budget, stream=None):
     sa = (M, K) if ta == "N" else (K, M)
     sb = (K, N) if tb == "N" else (N, K)
     A = pinned_from(seed, 0, *sa, synth.NORMAL)
@@ -29,7 +29,7 @@ def _pair(ooc, seed, ta, tb, M, N, K, alpha, beta, budget):
     C0 = np64(C1)
     rc = ooc.ooc_dgemm(ta, tb, M, N, K, alpha, A, sa[1], B, sb[1], beta, C1, N, budget)
     assert rc == 0, ooc.ooc_last_error()
-    rc = ooc.ooc_dgemm_noalloc(ta, tb, M, N, K, alpha, A, sa[1], B, sb[1], beta, C2, N, budget, None)
+    rc = ooc.ooc_dgemm_noalloc(ta, tb, M, N, K, alpha, A, sa[1], B, sb[1], beta, C2, N, budget, stream)
     assert rc == 0, ooc.ooc_last_error()
     return np64(C1), np64(C2), oracle.gemm(ta, tb, alpha, np64(A), np64(B), beta, C0)
 
@@ -53,3 +53,18 @@ def test_noalloc_rejects_budget_above_its_array(ooc):
                                ooc.OOC_NOALLOC_MAX_BYTES + 1, None)
     assert rc == ooc.OOC_ERR_INVALID_ARG
     assert "exceeds" in ooc.ooc_last_error()
+
+
+def test_noalloc_on_a_non_blocking_stream(ooc):
+    """The stream argument is what sets this entry point apart: all its copies, kernels and
+    the read of its error word run on the caller's stream.  Two calls in a row on a
+    non-blocking stream (which does not synchronise with the legacy default stream); the
+    error word the first call used must be cleared again for the second."""
+    import torch
+    s = torch.cuda.Stream()
+    ref1, got1, ora1 = _pair(ooc, 33, "T", "T", 600, 300, 700, 0.5, -2.0, 2 << 20, stream=s.cuda_stream)
+    assert oracle.rel_fro(got1, ref1) <= TOL
+    assert oracle.rel_fro(got1, ora1) <= TOL
+    ref2, got2, ora2 = _pair(ooc, 34, "N", "N", 257, 513, 1000, 1.0, 0.0, 4 << 20, stream=s.cuda_stream)
+    assert oracle.rel_fro(got2, ref2) <= TOL
+    assert oracle.rel_fro(got2, ora2) <= TOL
