@@ -493,6 +493,17 @@ int ooc_costmodel_set(const float* params, int64_t n);
  */
 int ooc_query_device(size_t* free_bytes, double* h2d_gbps, double* d2h_gbps);
 
+/*
+ * Measured FP64 peak of the current device in TFLOP/s: the paper quotes each
+ * device's FP64 peak beside its DGEMM results (Section V); this measures it
+ * with the instruction the FP64 tile kernel runs (mma.sync m8n8k4 f64, operands
+ * in registers, so only the FP64 pipe bounds it), the best of repeated
+ * launches over about `seconds` (0 < seconds <= 60; else OOC_ERR_INVALID_ARG).
+ * Allocates and frees a small output buffer; synchronous.  OOC_ERR_NO_DEVICE
+ * without an sm_103 device.
+ */
+int ooc_query_fp64_peak(double seconds, double* tflops);
+
 /* Name of a status code (static string). */
 const char* ooc_strerror(int code);
 

@@ -569,6 +569,17 @@ def ooc_query_device():
     return f.value, h.value, d.value
 
 
+def ooc_query_fp64_peak(seconds=1.0):
+    """C ABI ooc_query_fp64_peak: the device's measured FP64 (mma.sync f64) peak in TFLOP/s."""
+    lib = load()
+    f = lib.ooc_query_fp64_peak
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
+    t = ctypes.c_double(0)
+    _check(f(seconds, ctypes.byref(t)), "ooc_query_fp64_peak")
+    return t.value
+
+
 def ooc_strerror(code):
     return load().ooc_strerror(code).decode()
 

@@ -406,6 +406,7 @@ struct Dev {
     // Ozaki form for the in-HBM updates: digit-plane scratch (null: FP64 tiles)
     char* oz = nullptr;
     size_t oz_bytes = 0;
+    int oz_slices = kOzakiSlicesFactor;
 };
 
 // One in-HBM update C = alpha op(A) op(B) + beta C: the Ozaki form when the call
@@ -414,10 +415,10 @@ int dev_gemm(Dev& d, bool a_k, bool b_k, int64_t M, int64_t N, int64_t K, double
              const double* B, int64_t ldb, double beta, bool read_c, double* C, int64_t ldc, std::string& why,
              int tri = 0, int64_t tri_off = 0)
 {
-    if (d.oz && K > 0 && ozaki_device_scratch(M, N, K) <= d.oz_bytes) {
+    if (d.oz && K > 0 && ozaki_device_scratch(M, N, K, d.oz_slices) <= d.oz_bytes) {
         d.launches += 7;  // two splits of three kernels each, one tensor-core launch
-        return ozaki_gemm_device(a_k, b_k, M, N, K, alpha, A, lda, B, ldb, beta, read_c, C, ldc, d.oz, d.oz_bytes,
-                                 d.err, d.st, why, tri, tri_off);
+        return ozaki_gemm_device(a_k, b_k, M, N, K, alpha, A, lda, B, ldb, beta, read_c, C, ldc, d.oz_slices, d.oz,
+                                 d.oz_bytes, d.err, d.st, why, tri, tri_off);
     }
     ++d.launches;
     return launch_fp64_tile(a_k, b_k, M, N, K, alpha, A, lda, B, ldb, beta, read_c, C, ldc, d.err, d.st, why, tri,
@@ -641,6 +642,15 @@ struct Driver {
     {
         std::memset(&gemm_opts, 0, sizeof(gemm_opts));
         if (opts) gemm_opts = *opts;
+        if (gemm_opts.form == OOC_FORM_OZAKI) {
+            // the factors must track FP64's: 9 digits of 6 bits (54 bits) unless the caller chose
+            if (gemm_opts.slices == 0) gemm_opts.slices = kOzakiSlicesFactor;
+            if (gemm_opts.slices < 2 || gemm_opts.slices > kOzakiMaxSlices) {
+                why = "opts->slices must be 0 or 2.." + std::to_string(kOzakiMaxSlices);
+                return OOC_ERR_INVALID_ARG;
+            }
+            d.oz_slices = gemm_opts.slices;
+        }
         if (gemm_opts.workspace) {
             why = "the TRSM / Cholesky drivers allocate their own arena (opts->workspace must be NULL)";
             return OOC_ERR_INVALID_ARG;
@@ -724,6 +734,10 @@ struct Driver {
         stats->h2d_bytes = h2d;
         stats->d2h_bytes = d2h;
         stats->form = gemm_opts.form;
+        if (gemm_opts.form == OOC_FORM_OZAKI) {
+            stats->slices = gemm_opts.slices;
+            stats->products = gemm_opts.slices * (gemm_opts.slices + 1) / 2;
+        }
         stats->steps = steps;
         stats->device_bytes = (int64_t)bytes;
         stats->kernel_launches = launches + d.launches;
@@ -746,9 +760,9 @@ int64_t chunk_and_scratch(Driver& dr, char* region, size_t region_bytes, int64_t
     dr.d.oz = nullptr;
     dr.d.oz_bytes = 0;
     if (dr.gemm_opts.form == OOC_FORM_OZAKI) {
-        while (c > kSmall && bytes_of(c) + ozaki_device_scratch(t, c, t) > region_bytes)
+        while (c > kSmall && bytes_of(c) + ozaki_device_scratch(t, c, t, dr.d.oz_slices) > region_bytes)
             c = std::max<int64_t>(kSmall, c / 2 / 16 * 16);
-        if (bytes_of(c) + ozaki_device_scratch(t, c, t) <= region_bytes) {
+        if (bytes_of(c) + ozaki_device_scratch(t, c, t, dr.d.oz_slices) <= region_bytes) {
             dr.d.oz = region + bytes_of(c);
             dr.d.oz_bytes = region_bytes - bytes_of(c);
         }
@@ -994,7 +1008,8 @@ int ooc_dgetrf(int64_t N, double* A, int64_t lda, int64_t* ipiv, size_t device_b
     const size_t fixed = 256 + 4096 + lu_scratch + 8 * 1024;
     auto panel_bytes = [&](int64_t w) { return (size_t)N * round_up64(w, 16) * 8; };
     const bool oz = opts && opts->form == OOC_FORM_OZAKI;
-    auto oz_of = [&](int64_t w) { return oz ? ozaki_device_scratch(N, w, w) + 256 : (size_t)0; };
+    const int oz_s = oz && opts->slices > 0 ? opts->slices : kOzakiSlicesFactor;
+    auto oz_of = [&](int64_t w) { return oz ? ozaki_device_scratch(N, w, w, oz_s) + 256 : (size_t)0; };
     auto too_big = [&](int64_t w) {
         return fixed + panel_bytes(w) + oz_of(w) + (size_t)64 * round_up64(w, 16) * 8 + 512 > device_budget_bytes ||
                (size_t)(w * round_up64(w, 16) * 8 + 256 + 64 * 8 * round_up64(w, 16) + 4096) > device_budget_bytes;

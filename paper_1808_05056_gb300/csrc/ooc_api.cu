@@ -161,31 +161,34 @@ void ozaki_groups(TcProblem& P, int S)
 }
 
 namespace {
-constexpr int kOzakiSlices = 8;
 size_t al256(size_t x) { return (x + 255) / 256 * 256; }
 int64_t up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
-size_t side_bytes(int64_t rows, int64_t k_pad)
+size_t side_bytes(int64_t rows, int64_t k_pad, int S)
 {
     const int64_t rp = up(std::max<int64_t>(rows, 1), 128);
-    return al256((size_t)kOzakiSlices * rp * k_pad * 2) + al256((size_t)rp * 4) + al256((size_t)rp * 8);
+    return al256((size_t)S * rp * k_pad * 2) + al256((size_t)rp * 4) + al256((size_t)rp * 8);
 }
 }  // namespace
 
-size_t ozaki_device_scratch(int64_t M, int64_t N, int64_t K)
+size_t ozaki_device_scratch(int64_t M, int64_t N, int64_t K, int S)
 {
     const int64_t k_pad = up(std::max<int64_t>(K, 1), 64);
-    return side_bytes(M, k_pad) + side_bytes(N, k_pad);
+    return side_bytes(M, k_pad, S) + side_bytes(N, k_pad, S);
 }
 
 int ozaki_gemm_device(bool a_kmajor, bool b_kmajor, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
                       int64_t lda, const double* B, int64_t ldb, double beta, bool read_c, double* C, int64_t ldc,
-                      void* scratch, size_t scratch_bytes, int* err, void* stream, std::string& why, int tri,
+                      int S, void* scratch, size_t scratch_bytes, int* err, void* stream, std::string& why, int tri,
                       int64_t tri_off)
 {
     if (M <= 0 || N <= 0) return OOC_OK;
     if (K <= 0) return launch_fp64_tile(a_kmajor, b_kmajor, M, N, K, alpha, A, lda, B, ldb, beta, read_c, C, ldc,
                                         err, stream, why, tri, tri_off);
-    if (ozaki_device_scratch(M, N, K) > scratch_bytes) {
+    if (S < 2 || S > kOzakiMaxSlices) {
+        why = "Ozaki slice count out of range";
+        return OOC_ERR_INVALID_ARG;
+    }
+    if (ozaki_device_scratch(M, N, K, S) > scratch_bytes) {
         why = "Ozaki scratch too small";
         return OOC_ERR_BUDGET;
     }
@@ -203,21 +206,21 @@ int ozaki_gemm_device(bool a_kmajor, bool b_kmajor, int64_t M, int64_t N, int64_
     side[1] = {B, N, b_kmajor ? ldb : 1, b_kmajor ? 1 : ldb, nullptr, nullptr, nullptr, up(N, 128)};
     for (auto& sd : side) {
         sd.planes = base;
-        base += al256((size_t)kOzakiSlices * sd.rows_pad * k_pad * 2);
+        base += al256((size_t)S * sd.rows_pad * k_pad * 2);
         sd.exps = reinterpret_cast<int*>(base);
         base += al256((size_t)sd.rows_pad * 4);
         sd.rowmax = reinterpret_cast<unsigned long long*>(base);
         base += al256((size_t)sd.rows_pad * 8);
         const int rc = launch_split_ozaki(sd.X, sd.sr, sd.sk, (int)sd.rows, (int)K, (int)sd.rows_pad, (int)k_pad,
-                                          kOzakiSlices, kOzakiBeta, sd.planes, sd.exps, sd.rowmax, stream, why);
+                                          S, kOzakiBeta, sd.planes, sd.exps, sd.rowmax, stream, why);
         if (rc) return rc;
     }
     TcProblem P;
     P.M = M; P.N = N; P.k_pad = k_pad;
     P.chunk = kOzakiChunk;
-    P.a_planes = side[0].planes; P.a_rows_pad = side[0].rows_pad; P.a_nplanes = kOzakiSlices;
-    P.b_planes = side[1].planes; P.b_rows_pad = side[1].rows_pad; P.b_nplanes = kOzakiSlices;
-    ozaki_groups(P, kOzakiSlices);
+    P.a_planes = side[0].planes; P.a_rows_pad = side[0].rows_pad; P.a_nplanes = S;
+    P.b_planes = side[1].planes; P.b_rows_pad = side[1].rows_pad; P.b_nplanes = S;
+    ozaki_groups(P, S);
     P.row_exp = side[0].exps;
     P.col_exp = side[1].exps;
     P.alpha = alpha;

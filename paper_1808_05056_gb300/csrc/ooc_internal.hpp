@@ -242,13 +242,13 @@ struct TcProblem {
 
 int tc_max_groups();
 void ozaki_groups(TcProblem& P, int S);
-// C = alpha op(A) op(B) + beta C on device FP64 operands in the Ozaki form (8
+// C = alpha op(A) op(B) + beta C on device FP64 operands in the Ozaki form (S
 // digit planes per operand in `scratch`, at least ozaki_device_scratch bytes);
 // operand conventions as launch_fp64_tile.
-size_t ozaki_device_scratch(int64_t M, int64_t N, int64_t K);
+size_t ozaki_device_scratch(int64_t M, int64_t N, int64_t K, int S);
 int ozaki_gemm_device(bool a_kmajor, bool b_kmajor, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
                       int64_t lda, const double* B, int64_t ldb, double beta, bool read_c, double* C, int64_t ldc,
-                      void* scratch, size_t scratch_bytes, int* err, void* stream, std::string& why, int tri = 0,
+                      int S, void* scratch, size_t scratch_bytes, int* err, void* stream, std::string& why, int tri = 0,
                       int64_t tri_off = 0);
 int launch_tc_terms(const TcProblem& P, void* stream, std::string& why);
 int launch_split_bf16x3(const float* X, int64_t sr, int64_t sk, int rows, int K, int rows_pad, int k_pad,
@@ -261,6 +261,12 @@ int encode_map_3d_bf16(void* map_out, const void* base, uint64_t inner, uint64_t
 
 // Ozaki digit width and the largest K chunk whose digit products sum exactly in FP32
 constexpr int kOzakiBeta = 6;
+// digits per operand: 8 (48 bits) for the GEMM entry points unless opts->slices
+// asks otherwise; 9 (54 bits, FP64's 53-bit significand covered) for the
+// updates inside the factorizations, whose factors must track FP64's
+constexpr int kOzakiSlicesGemm = 8;
+constexpr int kOzakiSlicesFactor = 9;
+constexpr int kOzakiMaxSlices = 10;
 constexpr int kOzakiChunk = 4096;
 constexpr int kBf16x3Chunk = 128;
 

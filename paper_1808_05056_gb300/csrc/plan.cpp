@@ -58,7 +58,7 @@ FormModel form_model(int form, int es, int64_t K, int slices_opt)
         f.products = 6; f.slices = 3;
         f.rate = 1.2e15 / 6.0;
     } else {  // Ozaki
-        int s = slices_opt > 0 ? slices_opt : 8;
+        int s = slices_opt > 0 ? slices_opt : kOzakiSlicesGemm;
         f.tile_m = 128; f.tile_n = 128; f.ctas_per_sm = 1;
         f.slices = s; f.products = s * (s + 1) / 2;
         f.rate = 1.2e15 / f.products;
@@ -320,6 +320,10 @@ int make_plan(const PlanRequest& rq, Plan& p, std::string& why)
         return OOC_ERR_INVALID_ARG;
     }
     p.form = form;
+    if (form == OOC_FORM_OZAKI && rq.opts.slices != 0 && (rq.opts.slices < 2 || rq.opts.slices > kOzakiMaxSlices)) {
+        why = "opts->slices must be 0 or 2.." + std::to_string(kOzakiMaxSlices);
+        return OOC_ERR_INVALID_ARG;
+    }
     const FormModel f = form_model(form, rq.es, rq.K, rq.opts.slices);
     p.slices = f.slices; p.products = f.products;
     const int sms = device_sm_count();

@@ -18,6 +18,7 @@ import numpy as np  # noqa: E402
 import torch  # noqa: E402
 
 import bench  # noqa: E402
+import bounds  # noqa: E402
 import oracle  # noqa: E402
 import synth  # noqa: E402
 import paper_1808_05056_gb300 as P  # noqa: E402
@@ -71,13 +72,29 @@ def main(name):
         st = P.ooc_stats()
         rc = call("N", "N", M, N, K, alpha, A, K, B, N, beta, C, N, budget, P.make_opts(form=form_id), st)
         out["rc"] = rc
-        errs = []
+        errs, ratios = [], []
+        kchunks = max(1, -(-K // st.kb)) if st.kb else 1
         for (i, j), c0 in zip(blocks, cold):
             ref, _ = oracle.gemm_block("N", "N", i, j, 64, 64, K, alpha, A.numpy(), B.numpy(), beta,
                                        c0 if beta != 0 else None)
-            errs.append(oracle.rel_fro(C.numpy()[i:i + 64, j:j + 64], ref))
+            got = C.numpy()[i:i + 64, j:j + 64]
+            errs.append(oracle.rel_fro(got, ref))
+            # elementwise: each form's own componentwise bound (tests/bounds.py)
+            Ab = A.numpy()[i:i + 64, :].astype(np.float64)
+            Bb = B.numpy()[:, j:j + 64].astype(np.float64)
+            c0b = c0 if beta != 0 else None
+            if form == "ozaki":
+                bd = bounds.ozaki_bound(Ab, Bb, alpha, beta, c0b, st.slices, kchunks)
+            elif form == "bf16x3":
+                bd = bounds.bf16x3_bound(Ab, Bb, alpha, beta, c0b, kchunks)
+            else:
+                bd = None
+            if bd is not None:
+                ratios.append(bounds.worst_ratio(got, ref, bd))
         out.update(max_rel_fro=max(errs), tol=tol, samples=len(errs), blocks=st.blocks,
                    device_bytes=st.device_bytes, budget=budget)
+        if ratios:
+            out["max_elementwise_ratio"] = max(ratios)
     print(json.dumps(out), flush=True)
 
 

@@ -8,6 +8,11 @@ Ozaki (ooc_dgemm, OOC_FORM_OZAKI): FP64 operands, FP64-accurate: relative
 Frobenius error <= 1e-12 against the FP64 oracle, on inputs with a 10^8
 exponent spread (sign * 10^U(-4,4)).  Small-integer inputs are exact (their
 digits are exact and every digit product sums exactly in FP32).
+
+Besides the norm, every result is checked element by element against the bound each form's
+arithmetic gives (tests/bounds.py): BF16x3 relative to (|A||B|)_ij, Ozaki relative to the
+operand rows' and columns' largest entries (its digits are cut from each row's fixed-point
+value), so a wrong small entry cannot hide behind the large ones that dominate the norm.
 """
 import itertools
 
@@ -17,11 +22,23 @@ import torch
 
 import oracle
 import synth
+from bounds import bf16x3_bound, op, ozaki_bound, worst_ratio
 from gpu_util import np64, pinned, pinned_from
 
 pytestmark = pytest.mark.gpu
 TOL_BF16X3 = 1e-6
 TOL_OZAKI = 1e-12
+OZAKI_DIGITS = 8   # the GEMM entry points' default digit count
+
+
+def _elementwise(ooc, form, got, ref, A, B, ta, tb, alpha, beta, C0, kchunks=1, S=OZAKI_DIGITS):
+    Aop, Bop = op(np64(A), ta), op(np64(B), tb)
+    if form == ooc.OOC_FORM_BF16X3:
+        bound = bf16x3_bound(Aop, Bop, alpha, beta, C0, kchunks)
+    else:
+        bound = ozaki_bound(Aop, Bop, alpha, beta, C0, S, kchunks)
+    r = worst_ratio(got, ref, bound)
+    assert r <= 1.0, "elementwise error %.3g x its bound" % r
 
 
 def _run(ooc, form, ta, tb, M, N, K, alpha, beta, kind, param=0.0, budget=1 << 30, seed=40, c_nan=False):
@@ -42,7 +59,11 @@ def _run(ooc, form, ta, tb, M, N, K, alpha, beta, kind, param=0.0, budget=1 << 3
     rc = f(ta, tb, M, N, K, alpha, A, sa[1], B, sb[1], beta, C, N, budget, opts, st)
     assert rc == 0, ooc.ooc_last_error()
     ref = oracle.gemm(ta, tb, alpha, np64(A), np64(B), beta, None if beta == 0 else C0)
-    return np64(C), ref, st
+    got = np64(C)
+    if kind != synth.INTEGER:
+        _elementwise(ooc, form, got, ref, A, B, ta, tb, alpha, beta, None if beta == 0 else C0,
+                     kchunks=max(1, -(-K // st.kb)) if st.kb else 1)
+    return got, ref, st
 
 
 @pytest.mark.parametrize("ta,tb", list(itertools.product("NT", "NT")))
@@ -132,6 +153,7 @@ def test_forms_on_cta_pairs(ooc, form):
     assert rc == 0, ooc.ooc_last_error()
     ref = oracle.gemm("N", "N", 1.5, np64(A), np64(B), 0.5, C0)
     assert oracle.rel_fro(np64(C), ref) <= (TOL_BF16X3 if fp32 else TOL_OZAKI)
+    _elementwise(ooc, form, np64(C), ref, A, B, "N", "N", 1.5, 0.5, C0)
 
 
 @pytest.mark.parametrize("form", [3, 2])
@@ -154,3 +176,32 @@ def test_forms_with_k_chunks(ooc, form):
     assert st.kb == 256 and st.steps == 3 * 3 * 4
     ref = oracle.gemm("N", "N", 1.25, np64(A), np64(B), 0.5, C0)
     assert oracle.rel_fro(np64(C), ref) <= (TOL_BF16X3 if fp32 else TOL_OZAKI)
+    _elementwise(ooc, form, np64(C), ref, A, B, "N", "N", 1.25, 0.5, C0, kchunks=4)
+
+
+@pytest.mark.parametrize("S", [9, 10])
+def test_ozaki_more_digits(ooc, S):
+    """opts->slices above the default: more digit planes and products, the bound shrinks by
+    2^-6 per digit, and both checks still hold with it."""
+    M, N, K = 260, 200, 300
+    A = pinned_from(46, 0, M, K, synth.LOGSPREAD)
+    B = pinned_from(46, 1, K, N, synth.LOGSPREAD)
+    C = pinned_from(46, 2, M, N, synth.LOGSPREAD)
+    C0 = np64(C)
+    st = ooc.ooc_stats()
+    rc = ooc.ooc_dgemm("N", "N", M, N, K, 1.0, A, K, B, N, -1.0, C, N, 1 << 30,
+                       ooc.make_opts(form=ooc.OOC_FORM_OZAKI, slices=S), st)
+    assert rc == 0, ooc.ooc_last_error()
+    assert st.slices == S and st.products == S * (S + 1) // 2
+    ref = oracle.gemm("N", "N", 1.0, np64(A), np64(B), -1.0, C0)
+    assert oracle.rel_fro(np64(C), ref) <= TOL_OZAKI
+    _elementwise(ooc, ooc.OOC_FORM_OZAKI, np64(C), ref, A, B, "N", "N", 1.0, -1.0, C0, S=S)
+
+
+def test_ozaki_bad_digit_count(ooc):
+    A = pinned(8, 8, fill=1.0)
+    C = pinned(8, 8, fill=0.0)
+    for S in (1, 11):
+        rc = ooc.ooc_dgemm("N", "N", 8, 8, 8, 1.0, A, 8, A, 8, 0.0, C, 8, 1 << 20,
+                           ooc.make_opts(form=ooc.OOC_FORM_OZAKI, slices=S), None)
+        assert rc == ooc.OOC_ERR_INVALID_ARG

@@ -3,7 +3,9 @@
 Each configuration runs in a fresh process (tests/fullsize_check.py): tens of
 GiB of pinned host operands per configuration, freed when the process exits.
 Outputs are checked on sampled 64 x 64 blocks (and the four corner blocks,
-where tiles are ragged) against the CPU oracle, within each form's tolerance.
+where tiles are ragged) against the CPU oracle, within each form's tolerance,
+and for the split forms element by element within each form's componentwise
+bound (tests/bounds.py).
 """
 import json
 import os
@@ -25,5 +27,7 @@ def test_full_size_sampled_parity(ooc, config):
     print(json.dumps(res))
     assert res["rc"] == 0, res
     assert res["max_rel_fro"] <= res["tol"], res
+    # the split forms: every sampled element inside its form's componentwise bound
+    assert res.get("max_elementwise_ratio", 0.0) <= 1.0, res
     if "device_bytes" in res:
         assert res["device_bytes"] <= res["budget"]

@@ -79,6 +79,8 @@ def test_no_cpu_fallback_without_a_device():
     assert P.ooc_dgemm_batched([P.gemm_desc("N", "N", A, B, C)], 1 << 20) == nd
     assert P.ooc_dgemm_device("N", "N", 4, 4, 4, 1.0, 1, 4, 1, 4, 0.0, 1, 4) == nd
     assert P.ooc_dgemm_noalloc("N", "N", 4, 4, 4, 1.0, A, 4, B, 4, 0.0, C, 4, 1 << 20) == nd
+    with pytest.raises(RuntimeError):
+        P.ooc_query_fp64_peak(0.1)
     assert P.Session(4, 4, C, 4, 0.0, 1 << 20).rc == nd
     pipe = P.Pipe(P.MMOOC_PIPELINE)
     for name, v in dict(mb=4, nb=4, kb=4, ra=2, rb=2, rc=2, alpha=1.0, beta=0.0, beta_nz=0).items():
