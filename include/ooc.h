@@ -65,8 +65,6 @@ extern "C" {
 /* ---- plan selection flags (ooc_opts.flags) --------------------------- */
 #define OOC_PLAN_PAPER 1u  /* Section IV partitioner: equal h x w split, 2A + 1B + 2C buffers */
 #define OOC_PLAN_MODEL 4u  /* choose among candidates with the installed cost model (ooc_costmodel_set) */
-#define OOC_TC_PAIR 8u     /* tensor-core forms: 256 x 128 tiles on CTA pairs (tcgen05 cta_group::2);
-                              measured slower than the default 128 x 128 single-CTA tiles on GB300 */
 
 /*
  * Options; a zero-initialised struct means "choose automatically".

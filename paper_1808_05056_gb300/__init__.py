@@ -68,7 +68,6 @@ class ooc_gemm_desc(ctypes.Structure):
 
 OOC_BATCH_GRAPH = 2
 OOC_PLAN_MODEL = 4
-OOC_TC_PAIR = 8
 OOC_MLP_INPUTS = 16
 OOC_MLP_PARAMS = 5313
 

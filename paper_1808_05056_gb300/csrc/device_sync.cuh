@@ -88,6 +88,29 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* e
     }
 }
 
+// mbar_wait for threads that are not on the critical path (the epilogue warps
+// of the tile kernels): between unsuccessful tries the warp sleeps, so that
+// it does not take issue slots from the TMA and MMA threads of its SM while
+// it waits.  Same limit and error reporting as mbar_wait.
+__device__ __forceinline__ bool mbar_wait_backoff(uint64_t* bar, uint32_t parity, int* err, int code)
+{
+    const uint32_t a = smem_u32(bar);
+    if (mbar_try_wait(a, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    uint32_t ns = 32;
+#pragma unroll 1
+    while (true) {
+        __nanosleep(ns);
+        if (mbar_try_wait(a, parity)) return true;
+        if (ns < 256) ns <<= 1;
+        if (*reinterpret_cast<volatile int*>(err) != 0) return false;
+        if (globaltimer_ns() - t0 > kWaitLimitNs) {
+            atomicCAS(err, 0, code);
+            return false;
+        }
+    }
+}
+
 // 2-D TMA tile load into shared memory, completing on `bar` (transaction bytes).
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
                                             int32_t x, int32_t y)

@@ -483,7 +483,6 @@ int launch_split_tile(const Plan& p, const Op& op, Exec& x, const Operands& o, i
     P.ldc = p.ldc_dev;
     P.err = err;
     P.kblock = 64;
-    P.pair = (x.flags & OOC_TC_PAIR) != 0;
     if (p.block_class(op.i, op.j) == 2) {
         P.tri = p.tri;
         P.tri_off = p.block_off(op.i, op.j);

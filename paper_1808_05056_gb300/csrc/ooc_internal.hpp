@@ -235,7 +235,6 @@ struct TcProblem {
     int* err = nullptr;
     bool df32 = false;                 // two accumulators per group, double-float drain (BF16x3)
     int kblock = 64;                   // K block per pipeline stage: 64 or 32
-    bool pair = false;                 // CTA-pair (cta_group::2, 256-row) tiles when the device allows
     int tri = 0;                       // epilogue mask as in launch_fp64_tile
     int64_t tri_off = 0;
 };

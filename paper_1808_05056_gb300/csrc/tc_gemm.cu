@@ -4,10 +4,13 @@
 //   BF16x3 (FP32-accurate, ooc_sgemm): each FP32 operand is split into three
 //   bf16 pieces x = h + m + l (each piece the bf16 rounding of what is left),
 //   and C = sum of the six products hh, hm, mh, hl, mm, lh (the dropped ml, lm,
-//   ll are below 2^-24 relative).  hh and the five small products use two TMEM
-//   accumulators, drained every `chunk` of K (two K blocks) into a double-float
-//   FP32 pair per output with TwoSum, which keeps the tensor cores' one-ulp,
-//   round-toward-zero accumulator bias far below the 1e-6 target.
+//   ll are below 2^-24 relative).  The tensor cores round their FP32
+//   accumulator toward zero, so each accumulator addition is biased by up to
+//   one ulp: the leading product hh has its own accumulator, drained every
+//   `chunk` of K (two K blocks, 8 additions) into an unbiased double-float
+//   (hi, lo) pair per output with TwoSum; the five small products, 2^-8 of
+//   hh and below, share a second accumulator that is drained far less often
+//   (every kSmallChunks chunks, 2048 of K) straight into lo.
 //
 //   Ozaki (FP64-accurate, ooc_dgemm with OOC_FORM_OZAKI), after Ozaki, Ogita,
 //   Oishi and Rump's error-free splitting of matrix products: every row of A
@@ -20,20 +23,29 @@
 //   2^(-beta (s+t)), and the epilogue applies 2^(e_i + f_j), alpha and beta.
 //
 // Kernel shape (both forms): persistent CTAs, one per SM, tile 128 x 128.
-//   warp 0      TMA producer: for each (tile, K chunk, group, K block of 64
-//               or 32) loads the group's bf16 plane tiles (128 rows x the K
-//               block, 128- or 64-byte swizzle) into a ring of stages;
-//   warp 1      allocates all 512 TMEM columns (two buffers x two 128-column
-//               accumulators) and issues tcgen05.mma (M=128, N=128, K=16):
-//               pair 0 of the group into accumulator 0, the other pairs into
-//               accumulator 1, committing stage releases and buffer-full
+//   warp 0      TMA producer: for each (tile, K chunk, group, K block of 64)
+//               loads the group's bf16 plane tiles (128-byte swizzle) into a
+//               ring of stages;
+//   warp 1      allocates all 512 TMEM columns and issues tcgen05.mma (M=128,
+//               N=128, K=16), committing stage releases and accumulator-full
 //               events to mbarriers;
-//   warps 2-17  epilogue: read a finished accumulator with tcgen05.ld, add it
-//               (times the group weight) into FP64 (Ozaki) or double-float
-//               FP32 (BF16x3) registers, 32 columns per warp, release it, and
-//               after the last chunk write alpha*acc*2^(e_i+f_j) + beta*C_old.
-// The two buffers let the tensor cores run the next group while the epilogue
-// drains the previous one.  Every wait is bounded (device_sync.cuh).
+//   warps 2-17  epilogue: drain finished accumulators with tcgen05.ld into
+//               FP64 (Ozaki) or packed double-float FP32 (BF16x3) registers,
+//               32 columns of one row per thread, release them, and after the
+//               last chunk write alpha*acc*2^(e_i+f_j) + beta*C_old.
+// TMEM: Ozaki uses two buffers of two 128-column accumulators (the group's two
+// products), so the tensor cores run the next group while the epilogue drains
+// the previous one; BF16x3 uses three buffers for hh and one accumulator for
+// the small products.
+//
+// The single issuing thread keeps its per-stage work to the MMAs themselves
+// (descriptor offsets precomputed per group, ring positions advanced without
+// division): at 64 cycles per 128 x 128 x 16 MMA, anything more starves the
+// tensor pipe.  CTA pairs (cta_group::2, 256 x 128 tiles with half of each B
+// tile per CTA) were measured slower on GB300 for both forms (BF16x3 1216 vs
+// 1384, Ozaki 1337 vs 1374 bf16 TFLOP/s) and are not built.  Every wait is
+// bounded (device_sync.cuh); the epilogue warps wait with a sleep between
+// tries so that they leave the issue slots to the TMA and MMA threads.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -50,14 +62,16 @@ namespace ooc {
 
 namespace {
 
-constexpr int BM = 128, BN = 128;
-constexpr uint32_t RING_BYTES = 192u * 1024u;       // single-CTA stage ring
-constexpr uint32_t RING_BYTES_PAIR = 216u * 1024u;  // pair stage ring (three 72 KiB BF16x3 stages)
-constexpr int EPI_WARPS = 16;            // 4 per TMEM lane quadrant, 32 columns each
+constexpr int BM = 128, BN = 128, BK = 64;
+constexpr uint32_t A_TILE = BM * BK * 2u;             // 128 rows x 64 bf16 of K (16 KiB)
+constexpr uint32_t RING_BYTES = 192u * 1024u;         // two 96 KiB BF16x3 stages, four 48 KiB Ozaki stages
+constexpr int EPI_WARPS = 16;                         // 4 per TMEM lane quadrant, 32 columns each
 constexpr int THREADS = (2 + EPI_WARPS) * 32;
 constexpr int MAX_GROUPS = 64;
+constexpr int MAX_STAGES = 16;
 constexpr size_t SMEM_BYTES = 1024 + RING_BYTES + 1024;
-constexpr size_t SMEM_BYTES_PAIR = 1024 + RING_BYTES_PAIR + 1024;
+constexpr int kSmallChunks = 16;                      // BF16x3: small products drained every 16 chunks
+constexpr uint32_t kSmallCol = 384;                   // BF16x3: TMEM column of the small-product accumulator
 
 struct TcGroup {
     int8_t na, nb, np, pad0;
@@ -66,7 +80,7 @@ struct TcGroup {
     int8_t pa[6];
     int8_t pb[6];
     int16_t scale_exp;   // weight of accumulator 0 (pair 0)
-    int16_t scale_exp2;  // weight of accumulator 1 (pairs 1.., Ozaki)
+    int16_t scale_exp2;  // weight of accumulator 1 (pair 1, Ozaki)
     int16_t pad1[2];
 };
 static_assert(sizeof(TcGroup) == 32, "group record layout");
@@ -91,8 +105,8 @@ struct TcArgs {
 };
 
 // Tile order: groups of kRasterRows tile rows, column-major inside a group, so
-// that the ~152 tiles in flight at once span few rows and few columns and
-// share their A and B plane tiles in L2.
+// that the tiles in flight at once span few rows and few columns and share
+// their A and B plane tiles in L2.
 constexpr int kRasterRows = 8;
 __device__ __forceinline__ void tile_coords(int tile, int tiles_m, int tiles_n, int& tm, int& tn)
 {
@@ -115,237 +129,262 @@ __device__ __forceinline__ double scaled_f32_to_f64(uint32_t xb, int e)
     return __longlong_as_double((long long)(sign | ex | man));
 }
 
-// DF32 = true (BF16x3): the first pair of a group (the leading product) and the
-// other pairs use two separate TMEM accumulators, drained into an unbiased
-// double-float (hi, lo) FP32 pair per output with TwoSum; the tensor cores
-// round their FP32 accumulator toward zero, so each accumulator add is biased
-// by up to one ulp and the leading product must not absorb the small ones.
-// DF32 = false (Ozaki): each of the group's (at most two) pairs has its own
-// accumulator of exact integer partial sums, drained into FP64 with its
-// power-of-two weight; the two pairs share the A digit plane.
-// BK: K block of one stage (64 bf16, 128-byte swizzle).
-// PAIR: two CTAs of a cluster compute one 256 x 128 tile with cta_group::2
-// MMAs issued by rank 0: each CTA loads its 128 rows of every A plane tile and
-// 64 of the 128 rows of every B plane tile, so a CTA moves and reads a quarter
-// less per MMA than a single-CTA 128 x 128 tile and the ring holds a third
-// stage for BF16x3.  Rank 1's copies complete on rank 0's stage barriers; the
-// MMA completions are multicast to both CTAs; both CTAs' epilogues report a
-// drained accumulator to rank 0.
-template <bool DF32, int BK, bool PAIR>
+// Packed pairs of FP32 values (element 2j in the low half): Blackwell's f32x2
+// arithmetic does two of the drain's additions per instruction.
+__device__ __forceinline__ uint64_t f2add(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t f2sub(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t pack2(uint32_t lo, uint32_t hi) { return ((uint64_t)hi << 32) | lo; }
+__device__ __forceinline__ float unpack2(uint64_t v, int j) { return __uint_as_float((uint32_t)(v >> (32 * j))); }
+
+// ring position: slot and pass parity, advanced without division
+struct Ring {
+    int s = 0;
+    uint32_t ph = 0;
+    __device__ __forceinline__ void next(int n)
+    {
+        if (++s == n) { s = 0; ph ^= 1u; }
+    }
+};
+
+// BF16x3 drains of the small-product accumulator: every kSmallChunks chunks and
+// at the last chunk of a tile (both the MMA issuer and the epilogue use this)
+__device__ __forceinline__ bool small_drain_after(int c, int nchunks)
+{
+    return c == nchunks - 1 || (c % kSmallChunks) == kSmallChunks - 1;
+}
+
+template <bool DF32>
 __global__ void __launch_bounds__(THREADS, 1) tc_terms_kernel(const __grid_constant__ CUtensorMap tmA,
                                                               const __grid_constant__ CUtensorMap tmB,
                                                               const __grid_constant__ TcArgs p)
 {
-    constexpr uint32_t A_TILE = 128u * BK * 2u;                  // 128 rows x BK bf16
-    constexpr uint32_t B_TILE = (PAIR ? 64u : 128u) * BK * 2u;   // this CTA's rows of a B tile
-    constexpr uint32_t RING = PAIR ? RING_BYTES_PAIR : RING_BYTES;
-    constexpr int PM = PAIR ? 2 * BM : BM;                       // C rows per tile
-    constexpr uint32_t kAccCols = 2 * BN;  // TMEM columns of one buffer: accumulators 0 and 1
-    constexpr uint32_t kTmemCols = 2 * kAccCols;
+    constexpr uint32_t B_TILE = BN * BK * 2u;
+    constexpr int NBUF = DF32 ? 3 : 2;                            // accumulator buffers in TMEM
+    constexpr uint32_t BUF_COLS = DF32 ? BN : 2 * BN;
+    constexpr uint32_t kTmemCols = 512;
+    constexpr int NPMAX = DF32 ? 6 : 2;
+    constexpr int KSTEPS = BK / 16;
+    constexpr uint32_t kArrivals = EPI_WARPS;                     // epilogue warps releasing a buffer
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* ring = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                            ~uintptr_t(1023));
-    uint64_t* full = reinterpret_cast<uint64_t*>(ring + RING);
-    uint64_t* empty = full + 16;
-    uint64_t* acc_full = empty + 16;
-    uint64_t* acc_empty = acc_full + 2;
-    uint64_t* drain = acc_empty + 2;
+    uint64_t* full = reinterpret_cast<uint64_t*>(ring + RING_BYTES);
+    uint64_t* empty = full + MAX_STAGES;
+    uint64_t* acc_full = empty + MAX_STAGES;
+    uint64_t* acc_empty = acc_full + 4;
+    uint64_t* small_full = acc_empty + 4;
+    uint64_t* small_empty = small_full + 1;
+    uint64_t* drain = small_empty + 1;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t rank = PAIR ? cluster_ctarank() : 0u;
-    const bool leader = rank == 0;
-    const int unit0 = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;  // tile-walking unit (CTA or pair)
-    const int nunits = PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
     if (warp == 1) {
-        if constexpr (PAIR) {
-            tmem_alloc_pair(tmem_slot, kTmemCols);
-            tmem_relinquish_pair();
-        } else {
-            tmem_alloc(tmem_slot, kTmemCols);
-            tmem_relinquish();
-        }
+        tmem_alloc(tmem_slot, kTmemCols);
+        tmem_relinquish();
     }
     if (threadIdx.x == 0) {
         for (int s = 0; s < p.nstages; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < NBUF; ++b) {
             mbar_init(&acc_full[b], 1);
-            mbar_init(&acc_empty[b], EPI_WARPS * (PAIR ? 2 : 1));
+            mbar_init(&acc_empty[b], kArrivals);
         }
+        mbar_init(small_full, 1);
+        mbar_init(small_empty, kArrivals);
         mbar_init(drain, 1);
         mbar_fence_init();
     }
     tc_fence_before();
-    if constexpr (PAIR) cluster_sync_all(); else __syncthreads();
+    __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
 
-    const int64_t my_tiles = p.tiles > unit0 ? (p.tiles - 1 - unit0) / nunits + 1 : 0;
+    const int64_t my_tiles =
+        p.tiles > (int)blockIdx.x ? (p.tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
 
     if (warp == 0) {
-        // ------------------------------------------------ TMA producer (each CTA loads its own halves)
+        // ------------------------------------------------ TMA producer
         if (lane == 0) {
             tma_prefetch_desc(&tmA);
             tma_prefetch_desc(&tmB);
-            uint32_t it = 0;
+            Ring r;
+            uint32_t issued = 0;
             bool ok = true;
             for (int64_t tl = 0; tl < my_tiles && ok; ++tl) {
-                const int tile = unit0 + (int)tl * nunits;
+                const int tile = (int)blockIdx.x + (int)tl * (int)gridDim.x;
                 int tm, tn;
                 tile_coords(tile, p.tiles_m, p.tiles_n, tm, tn);
-                const int arow = tm * PM + (int)rank * BM;
-                const int brow = tn * BN + (PAIR ? (int)rank * (BN / 2) : 0);
+                const int arow = tm * BM, brow = tn * BN;
                 for (int c = 0; c < p.nchunks && ok; ++c) {
                     const int kb0 = c * p.chunk_kblocks, kb1 = min(p.kblocks, kb0 + p.chunk_kblocks);
                     for (int gi = 0; gi < p.ngroups && ok; ++gi) {
                         const TcGroup& g = p.g[gi];
-                        for (int kb = kb0; kb < kb1; ++kb, ++it) {
-                            const int s = (int)(it % (uint32_t)p.nstages);
-                            const uint32_t ph = (it / (uint32_t)p.nstages) & 1u;
-                            if (!mbar_wait(&empty[s], ph ^ 1u, p.err, kErrWaitEmpty)) { ok = false; break; }
-                            unsigned char* st = ring + (size_t)s * p.stage_bytes;
-                            const uint32_t bytes = (uint32_t)g.na * A_TILE + (uint32_t)g.nb * B_TILE;
-                            if constexpr (PAIR) {
-                                // rank 0's barrier counts both CTAs' bytes; both CTAs' copies complete on it
-                                if (leader) mbar_arrive_expect_tx(&full[s], 2u * bytes);
-                                const uint32_t bar = mapa_shared(smem_u32(&full[s]), 0);
-                                for (int a = 0; a < g.na; ++a)
-                                    tma_load_3d_pair(st + a * A_TILE, &tmA, bar, kb * BK, arow, g.aplane[a]);
-                                for (int b = 0; b < g.nb; ++b)
-                                    tma_load_3d_pair(st + g.na * A_TILE + b * B_TILE, &tmB, bar, kb * BK, brow,
-                                                     g.bplane[b]);
-                            } else {
-                                mbar_arrive_expect_tx(&full[s], bytes);
-                                for (int a = 0; a < g.na; ++a)
-                                    tma_load_3d(st + a * A_TILE, &tmA, &full[s], kb * BK, arow, g.aplane[a]);
-                                for (int b = 0; b < g.nb; ++b)
-                                    tma_load_3d(st + g.na * A_TILE + b * B_TILE, &tmB, &full[s], kb * BK, brow,
-                                                g.bplane[b]);
-                            }
+                        const int na = g.na, nb = g.nb;
+                        const uint32_t bytes = (uint32_t)na * A_TILE + (uint32_t)nb * B_TILE;
+                        for (int kb = kb0; kb < kb1; ++kb) {
+                            if (!mbar_wait(&empty[r.s], r.ph ^ 1u, p.err, kErrWaitEmpty)) { ok = false; break; }
+                            unsigned char* st = ring + (size_t)r.s * p.stage_bytes;
+                            mbar_arrive_expect_tx(&full[r.s], bytes);
+                            for (int a = 0; a < na; ++a)
+                                tma_load_3d(st + a * A_TILE, &tmA, &full[r.s], kb * BK, arow, g.aplane[a]);
+                            for (int b = 0; b < nb; ++b)
+                                tma_load_3d(st + na * A_TILE + b * B_TILE, &tmB, &full[r.s], kb * BK, brow,
+                                            g.bplane[b]);
+                            r.next(p.nstages);
+                            ++issued;
                         }
                     }
                 }
             }
-            if (!ok && (!PAIR || leader)) {
+            if (!ok) {
                 // let the copies already issued land before the CTA exits
-                const uint32_t first = it > (uint32_t)p.nstages ? it - (uint32_t)p.nstages : 0u;
-                for (uint32_t q = first; q < it; ++q) {
-                    const int s = (int)(q % (uint32_t)p.nstages);
+                const uint32_t n = min(issued, (uint32_t)p.nstages);
+                for (uint32_t q = 0; q < n; ++q) {
+                    int s = r.s - 1 - (int)q;
+                    uint32_t ph = r.ph;
+                    while (s < 0) { s += p.nstages; ph ^= 1u; }
                     const uint64_t t0 = globaltimer_ns();
-                    while (!mbar_try_wait(smem_u32(&full[s]), (q / (uint32_t)p.nstages) & 1u) &&
-                           globaltimer_ns() - t0 < kWaitLimitNs) {
+                    while (!mbar_try_wait(smem_u32(&full[s]), ph) && globaltimer_ns() - t0 < kWaitLimitNs) {
                     }
                 }
             }
         }
     } else if (warp == 1) {
-        // ------------------------------------------------ MMA issuer (rank 0 of a pair)
-        if (lane == 0 && leader) {
-            const uint32_t idesc = idesc_bf16_f32(PM, BN);
-            uint32_t it = 0, unit = 0;
+        // ------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16_f32(BM, BN);
+            Ring r, b;
+            uint32_t small_drains = 0;   // BF16x3: small-accumulator drains committed so far
+            bool small_pending = false;  // a drain committed and not yet released by the epilogue
             bool ok = true;
             for (int64_t tl = 0; tl < my_tiles && ok; ++tl) {
+                uint32_t small_acc = 0;  // BF16x3: accumulate flag of the small-product accumulator
                 for (int c = 0; c < p.nchunks && ok; ++c) {
                     const int kb0 = c * p.chunk_kblocks, kb1 = min(p.kblocks, kb0 + p.chunk_kblocks);
-                    for (int gi = 0; gi < p.ngroups && ok; ++gi, ++unit) {
+                    for (int gi = 0; gi < p.ngroups && ok; ++gi) {
                         const TcGroup& g = p.g[gi];
-                        const int buf = (int)(unit & 1u);
-                        if (!mbar_wait(&acc_empty[buf], ((unit >> 1) & 1u) ^ 1u, p.err, kErrWaitAcc)) {
-                            ok = false;
-                            break;
-                        }
-                        tc_fence_after();
-                        const uint32_t d_tmem = tmem_base + (uint32_t)buf * kAccCols;
-                        uint32_t accumulate = 0, accumulate2 = 0;
-                        for (int kb = kb0; kb < kb1; ++kb, ++it) {
-                            const int s = (int)(it % (uint32_t)p.nstages);
-                            if (!mbar_wait(&full[s], (it / (uint32_t)p.nstages) & 1u, p.err, kErrWaitFull)) {
-                                ok = false;
-                                break;
-                            }
-                            tc_fence_after();
-                            const uint32_t st = smem_u32(ring + (size_t)s * p.stage_bytes);
-                            for (int q = 0; q < g.np; ++q) {
-                                const uint32_t a0 = st + (uint32_t)g.pa[q] * A_TILE;
-                                const uint32_t b0 = st + (uint32_t)g.na * A_TILE + (uint32_t)g.pb[q] * B_TILE;
-                                const bool second = q > 0;
-                                const uint32_t d = second ? d_tmem + BN : d_tmem;
+                        // descriptor offsets of the group's pairs (16-byte units)
+                        uint32_t aoff[NPMAX], boff[NPMAX];
+                        const int np = g.np;
+                        const uint32_t bbase = (uint32_t)g.na * A_TILE;
 #pragma unroll
-                                for (int k = 0; k < BK / 16; ++k) {
-                                    const uint64_t da = sw128_kmajor_desc(a0 + k * 32);
-                                    const uint64_t db = sw128_kmajor_desc(b0 + k * 32);
-                                    if constexpr (PAIR)
-                                        tc_mma_bf16_pair(d, da, db, idesc, second ? accumulate2 : accumulate);
-                                    else
-                                        tc_mma_bf16(d, da, db, idesc, second ? accumulate2 : accumulate);
-                                    if (second) accumulate2 = 1; else accumulate = 1;
+                        for (int q = 0; q < NPMAX; ++q) {
+                            const int src = q < np ? q : 0;
+                            aoff[q] = ((uint32_t)g.pa[src] * A_TILE) >> 4;
+                            boff[q] = (bbase + (uint32_t)g.pb[src] * B_TILE) >> 4;
+                        }
+                        if (!mbar_wait(&acc_empty[b.s], b.ph ^ 1u, p.err, kErrWaitAcc)) { ok = false; break; }
+                        tc_fence_after();
+                        const uint32_t d0 = tmem_base + (uint32_t)b.s * BUF_COLS;
+                        uint32_t acc0 = 0, acc1 = 0;
+                        for (int kb = kb0; kb < kb1; ++kb) {
+                            if (!mbar_wait(&full[r.s], r.ph, p.err, kErrWaitFull)) { ok = false; break; }
+                            tc_fence_after();
+                            const uint64_t dst = sw128_kmajor_desc(smem_u32(ring + (size_t)r.s * p.stage_bytes));
+                            if constexpr (DF32) {
+                                if (small_pending) {
+                                    // the epilogue has read the small accumulator before it restarts
+                                    if (!mbar_wait(small_empty, (small_drains - 1) & 1u, p.err, kErrWaitAcc)) {
+                                        ok = false;
+                                        break;
+                                    }
+                                    tc_fence_after();
+                                    small_pending = false;
                                 }
                             }
-                            if constexpr (PAIR) tc_commit_pair(&empty[s], 3); else tc_commit(&empty[s]);
+#pragma unroll
+                            for (int q = 0; q < NPMAX; ++q) {
+                                if (q < np) {
+                                    // DF32: pair 0 (hh) into buffer d0, pairs 1.. into the small accumulator;
+                                    // exact: pair q into accumulator q of the buffer
+                                    const uint32_t d = DF32 ? (q == 0 ? d0 : tmem_base + kSmallCol)
+                                                            : (q == 0 ? d0 : d0 + BN);
+                                    uint32_t& flag = DF32 ? (q == 0 ? acc0 : small_acc) : (q == 0 ? acc0 : acc1);
+                                    const uint64_t da = dst + aoff[q], db = dst + boff[q];
+#pragma unroll
+                                    for (int k = 0; k < KSTEPS; ++k) {
+                                        const uint32_t f = k > 0 ? 1u : flag;
+                                        tc_mma_bf16(d, da + 2 * k, db + 2 * k, idesc, f);
+                                    }
+                                    flag = 1u;
+                                }
+                            }
+                            tc_commit(&empty[r.s]);
+                            r.next(p.nstages);
                         }
-                        if (ok) {
-                            if constexpr (PAIR) tc_commit_pair(&acc_full[buf], 3); else tc_commit(&acc_full[buf]);
+                        if (!ok) break;
+                        tc_commit(&acc_full[b.s]);
+                        b.next(NBUF);
+                        if constexpr (DF32) {
+                            if (small_drain_after(c, p.nchunks)) {
+                                tc_commit(small_full);
+                                ++small_drains;
+                                small_pending = true;
+                                small_acc = 0;
+                            }
                         }
                     }
                 }
             }
             // every MMA issued so far has completed before TMEM is released
-            if constexpr (PAIR) tc_commit_pair(drain, 1); else tc_commit(drain);
+            tc_commit(drain);
             const uint64_t t0 = globaltimer_ns();
             while (!mbar_try_wait(smem_u32(drain), 0u) && globaltimer_ns() - t0 < kWaitLimitNs) {
             }
         }
     } else {
         // ------------------------------------------------ epilogue warps
-        const int q = warp & 3;                 // TMEM lane quadrant this warp may access
+        const int q4 = warp & 3;                 // TMEM lane quadrant this warp may access
         const int quarter = (warp - 2) >> 2;    // column quarter of the tile
-        const int row_in_tile = (int)rank * BM + q * 32 + lane;
-        const uint32_t lane_off = (uint32_t)(q * 32) << 16;
-        // DF32: a double-float (hi, lo) per output; FP64: one double per output
-        float hi[DF32 ? 32 : 1], lo[DF32 ? 32 : 1];
+        const int row_in_tile = q4 * 32 + lane;
+        const uint32_t lane_off = (uint32_t)(q4 * 32) << 16;
+        // DF32: a packed double-float (hi, lo) per output; exact: one double per output
+        uint64_t hi2[DF32 ? 16 : 1], lo2[DF32 ? 16 : 1];
         double acc[DF32 ? 1 : 32];
 #pragma unroll
-        for (int j = 0; j < (DF32 ? 32 : 1); ++j) hi[j] = lo[j] = 0.f;
+        for (int j = 0; j < (DF32 ? 16 : 1); ++j) hi2[j] = lo2[j] = 0ull;
 #pragma unroll
         for (int j = 0; j < (DF32 ? 1 : 32); ++j) acc[j] = 0.0;
-        uint32_t unit = 0;
+        Ring b;
+        uint32_t small_drains = 0;
         bool ok = true;
         for (int64_t tl = 0; tl < my_tiles && ok; ++tl) {
-            const int tile = unit0 + (int)tl * nunits;
+            const int tile = (int)blockIdx.x + (int)tl * (int)gridDim.x;
             int tm, tn;
             tile_coords(tile, p.tiles_m, p.tiles_n, tm, tn);
             for (int c = 0; c < p.nchunks && ok; ++c) {
-                for (int gi = 0; gi < p.ngroups; ++gi, ++unit) {
-                    const int buf = (int)(unit & 1u);
-                    if (!mbar_wait(&acc_full[buf], (unit >> 1) & 1u, p.err, kErrWaitMma)) { ok = false; break; }
+                for (int gi = 0; gi < p.ngroups; ++gi) {
+                    if (!mbar_wait_backoff(&acc_full[b.s], b.ph, p.err, kErrWaitMma)) { ok = false; break; }
                     tc_fence_after();
-                    const uint32_t t0 = tmem_base + lane_off + (uint32_t)buf * kAccCols + (uint32_t)(quarter * 32);
+                    const uint32_t t0 = tmem_base + lane_off + (uint32_t)b.s * BUF_COLS + (uint32_t)(quarter * 32);
                     if constexpr (DF32) {
-                        const bool has_small = p.g[gi].np > 1;
 #pragma unroll
-                        for (int cc = 0; cc < 2; ++cc) {
-                            uint32_t v[16];
-                            tmem_ld_32x32b_x16(t0 + cc * 16, v);
+                        for (int cc = 0; cc < 4; ++cc) {
+                            uint32_t v[8];
+                            tmem_ld_32x32b_x8(t0 + cc * 8, v);
                             tmem_wait_ld();
 #pragma unroll
-                            for (int j = 0; j < 16; ++j) {
-                                const int o = cc * 16 + j;
-                                const float x = __uint_as_float(v[j]);
-                                // TwoSum: hi + x = sum + e exactly
-                                const float sum = __fadd_rn(hi[o], x);
-                                const float bp = __fsub_rn(sum, hi[o]);
-                                const float e = __fadd_rn(__fsub_rn(hi[o], __fsub_rn(sum, bp)), __fsub_rn(x, bp));
-                                hi[o] = sum;
-                                lo[o] = __fadd_rn(lo[o], e);
-                            }
-                            if (has_small) {
-                                tmem_ld_32x32b_x16(t0 + BN + cc * 16, v);
-                                tmem_wait_ld();
-#pragma unroll
-                                for (int j = 0; j < 16; ++j) lo[cc * 16 + j] = __fadd_rn(lo[cc * 16 + j], __uint_as_float(v[j]));
+                            for (int j = 0; j < 4; ++j) {
+                                // TwoSum on pairs: hi + x = sum + e exactly, e added into lo
+                                uint64_t& h = hi2[cc * 4 + j];
+                                const uint64_t x = pack2(v[2 * j], v[2 * j + 1]);
+                                const uint64_t sum = f2add(h, x);
+                                const uint64_t bp = f2sub(sum, h);
+                                const uint64_t e = f2add(f2sub(h, f2sub(sum, bp)), f2sub(x, bp));
+                                h = sum;
+                                lo2[cc * 4 + j] = f2add(lo2[cc * 4 + j], e);
                             }
                         }
                     } else {
@@ -368,28 +407,53 @@ __global__ void __launch_bounds__(THREADS, 1) tc_terms_kernel(const __grid_const
                     }
                     tc_fence_before();
                     __syncwarp();
-                    if (lane == 0) {
-                        if constexpr (PAIR) mbar_arrive_cluster(mapa_shared(smem_u32(&acc_empty[buf]), 0));
-                        else mbar_arrive(&acc_empty[buf]);
+                    if (lane == 0) mbar_arrive(&acc_empty[b.s]);
+                    b.next(NBUF);
+                    if constexpr (DF32) {
+                        if (small_drain_after(c, p.nchunks)) {
+                            // the small products (2^-8 of hh and below) go straight into lo
+                            if (!mbar_wait_backoff(small_full, small_drains & 1u, p.err, kErrWaitMma)) {
+                                ok = false;
+                                break;
+                            }
+                            tc_fence_after();
+                            const uint32_t ts = tmem_base + lane_off + kSmallCol + (uint32_t)(quarter * 32);
+#pragma unroll
+                            for (int cc = 0; cc < 4; ++cc) {
+                                uint32_t v[8];
+                                tmem_ld_32x32b_x8(ts + cc * 8, v);
+                                tmem_wait_ld();
+#pragma unroll
+                                for (int j = 0; j < 4; ++j)
+                                    lo2[cc * 4 + j] = f2add(lo2[cc * 4 + j], pack2(v[2 * j], v[2 * j + 1]));
+                            }
+                            tc_fence_before();
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive(small_empty);
+                            ++small_drains;
+                        }
                     }
                 }
             }
             if (!ok) break;
             // final epilogue of this tile
-            const int64_t row = (int64_t)tm * PM + row_in_tile;
+            const int64_t row = (int64_t)tm * BM + row_in_tile;
             const int64_t col0 = (int64_t)tn * BN + quarter * 32;
             if (row < p.M) {
-                const int re = p.row_exp ? p.row_exp[row] : 0;
+                const int re = (!DF32 && p.row_exp) ? p.row_exp[row] : 0;
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
                     const int64_t col = col0 + j;
                     const bool keep = p.tri == 0 || (p.tri == 1 ? col - row <= p.tri_off : col - row >= p.tri_off);
                     if (col < p.N && keep) {
-                        double a;
-                        if constexpr (DF32) a = (double)hi[j] + (double)lo[j];
-                        else a = acc[j];
-                        const int ce = p.col_exp ? p.col_exp[col] : 0;
-                        double v = p.alpha * ldexp(a, re + ce);
+                        double v;
+                        if constexpr (DF32) {
+                            // no operand scaling in this form
+                            v = p.alpha * ((double)unpack2(hi2[j >> 1], j & 1) + (double)unpack2(lo2[j >> 1], j & 1));
+                        } else {
+                            const int ce = p.col_exp ? p.col_exp[col] : 0;
+                            v = p.alpha * ldexp(acc[j], re + ce);
+                        }
                         if (p.c_fp32) {
                             float* cp = static_cast<float*>(p.C) + row * p.ldc + col;
                             if (p.read_c) v = fma(p.beta, (double)*cp, v);
@@ -403,17 +467,16 @@ __global__ void __launch_bounds__(THREADS, 1) tc_terms_kernel(const __grid_const
                 }
             }
 #pragma unroll
-            for (int j = 0; j < (DF32 ? 32 : 1); ++j) hi[j] = lo[j] = 0.f;
+            for (int j = 0; j < (DF32 ? 16 : 1); ++j) hi2[j] = lo2[j] = 0ull;
 #pragma unroll
             for (int j = 0; j < (DF32 ? 1 : 32); ++j) acc[j] = 0.0;
         }
     }
     tc_fence_before();
-    if constexpr (PAIR) cluster_sync_all(); else __syncthreads();
+    __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        if constexpr (PAIR) tmem_dealloc_pair(tmem_base, kTmemCols);
-        else tmem_dealloc(tmem_base, kTmemCols);
+        tmem_dealloc(tmem_base, kTmemCols);
     }
 }
 
@@ -543,7 +606,6 @@ __global__ void __launch_bounds__(256) split_ozaki_kernel(const double* __restri
 
 std::once_flag g_attr_once;
 int g_sms = 0;
-int g_pairs = 0;  // resident CTA pairs of the pair kernel (0: pairs unavailable)
 
 }  // namespace
 
@@ -584,42 +646,12 @@ int launch_tc_terms(const TcProblem& P, void* stream, std::string& why)
     if (P.M <= 0 || P.N <= 0) return OOC_OK;
     if (P.ngroups <= 0 || P.ngroups > MAX_GROUPS) { why = "bad group count"; return OOC_ERR_INVALID_ARG; }
     std::call_once(g_attr_once, [] {
-        cudaFuncSetAttribute(tc_terms_kernel<true, 64, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)SMEM_BYTES);
-        cudaFuncSetAttribute(tc_terms_kernel<false, 64, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)SMEM_BYTES);
-        cudaFuncSetAttribute(tc_terms_kernel<true, 64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)SMEM_BYTES_PAIR);
-        cudaFuncSetAttribute(tc_terms_kernel<false, 64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)SMEM_BYTES_PAIR);
+        cudaFuncSetAttribute(tc_terms_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+        cudaFuncSetAttribute(tc_terms_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
         g_sms = device_sm_count();
-        // CTA pairs that can be resident at once (clusters are placed inside GPCs)
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(2 * 76);
-        cfg.blockDim = dim3(THREADS);
-        cfg.dynamicSmemBytes = SMEM_BYTES_PAIR;
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = 2;
-        at[0].val.clusterDim.y = 1;
-        at[0].val.clusterDim.z = 1;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-        int n = 0;
-        if (cudaOccupancyMaxActiveClusters(&n, tc_terms_kernel<true, 64, true>, &cfg) != cudaSuccess) {
-            cudaGetLastError();
-            n = 0;
-        }
-        g_pairs = n;
     });
-    // 64-wide K blocks (128-byte swizzle) measured faster than 32-wide ones for
-    // both forms on GB300 (BF16x3 166 vs 136, Ozaki 28 vs 18 logical TFLOP/s)
-    const int BK = 64;
     if (P.kblock != BK) { why = "only 64-wide K blocks are built"; return OOC_ERR_INVALID_ARG; }
-    const bool pair = P.pair && g_pairs > 0;
-    const uint32_t A_TILE = 128u * (uint32_t)BK * 2u;
-    const uint32_t B_TILE = (pair ? 64u : 128u) * (uint32_t)BK * 2u;
-    const int PM = pair ? 2 * BM : BM;
+    const uint32_t B_TILE = BN * BK * 2u;
     TcArgs a;
     std::memset(&a, 0, sizeof(a));
     a.M = (int)P.M; a.N = (int)P.N;
@@ -629,7 +661,7 @@ int launch_tc_terms(const TcProblem& P, void* stream, std::string& why)
     a.nchunks = (a.kblocks + a.chunk_kblocks - 1) / a.chunk_kblocks;
     a.ngroups = P.ngroups;
     a.tiles_n = (int)((P.N + BN - 1) / BN);
-    a.tiles_m = (int)((P.M + PM - 1) / PM);
+    a.tiles_m = (int)((P.M + BM - 1) / BM);
     a.tiles = a.tiles_m * a.tiles_n;
     uint32_t max_stage = 0;
     for (int g = 0; g < P.ngroups; ++g) {
@@ -639,6 +671,11 @@ int launch_tc_terms(const TcProblem& P, void* stream, std::string& why)
             why = "bad group shape";
             return OOC_ERR_INVALID_ARG;
         }
+        for (int q = 0; q < s.np; ++q)
+            if (s.pa[q] < 0 || s.pa[q] >= s.na || s.pb[q] < 0 || s.pb[q] >= s.nb) {
+                why = "group pair index outside its loaded planes";
+                return OOC_ERR_INVALID_ARG;
+            }
         d.na = (int8_t)s.na; d.nb = (int8_t)s.nb; d.np = (int8_t)s.np;
         for (int i = 0; i < 4; ++i) { d.aplane[i] = (int8_t)s.aplane[i]; d.bplane[i] = (int8_t)s.bplane[i]; }
         for (int i = 0; i < 6; ++i) { d.pa[i] = (int8_t)s.pa[i]; d.pb[i] = (int8_t)s.pb[i]; }
@@ -651,7 +688,7 @@ int launch_tc_terms(const TcProblem& P, void* stream, std::string& why)
         max_stage = std::max(max_stage, (uint32_t)s.na * A_TILE + (uint32_t)s.nb * B_TILE);
     }
     a.stage_bytes = max_stage;
-    a.nstages = std::min<int>(16, (int)((pair ? RING_BYTES_PAIR : RING_BYTES) / a.stage_bytes));  // 16 barrier slots
+    a.nstages = std::min<int>(MAX_STAGES, (int)(RING_BYTES / a.stage_bytes));
     if (a.nstages < 2) { why = "stage ring too small"; return OOC_ERR_INVALID_ARG; }
     a.alpha = P.alpha; a.beta = P.beta;
     a.read_c = P.read_c ? 1 : 0; a.c_fp32 = P.c_fp32 ? 1 : 0;
@@ -664,38 +701,18 @@ int launch_tc_terms(const TcProblem& P, void* stream, std::string& why)
     std::memset(&ma, 0, sizeof(ma));
     std::memset(&mb, 0, sizeof(mb));
     if (a.kblocks > 0) {  // K == 0 runs the epilogue only (C = beta * C)
-        // rows past the padded planes (the last pair tile) read as zeros from TMA
         int rc = encode_map_3d_bf16(&ma, P.a_planes, (uint64_t)P.k_pad, (uint64_t)P.a_rows_pad,
                                     (uint64_t)P.a_nplanes, BK, BM, why);
         if (rc) return rc;
         rc = encode_map_3d_bf16(&mb, P.b_planes, (uint64_t)P.k_pad, (uint64_t)P.b_rows_pad, (uint64_t)P.b_nplanes,
-                                BK, pair ? BN / 2 : BN, why);
+                                BK, BN, why);
         if (rc) return rc;
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    cudaError_t e;
-    if (pair) {
-        const int pairs = std::min(a.tiles, g_pairs);
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3((unsigned)(2 * pairs));
-        cfg.blockDim = dim3(THREADS);
-        cfg.dynamicSmemBytes = SMEM_BYTES_PAIR;
-        cfg.stream = st;
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = 2;
-        at[0].val.clusterDim.y = 1;
-        at[0].val.clusterDim.z = 1;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-        e = P.df32 ? cudaLaunchKernelEx(&cfg, tc_terms_kernel<true, 64, true>, ma, mb, a)
-                   : cudaLaunchKernelEx(&cfg, tc_terms_kernel<false, 64, true>, ma, mb, a);
-    } else {
-        const int grid = std::min(a.tiles, g_sms > 0 ? g_sms : 152);
-        if (P.df32) tc_terms_kernel<true, 64, false><<<grid, THREADS, SMEM_BYTES, st>>>(ma, mb, a);
-        else tc_terms_kernel<false, 64, false><<<grid, THREADS, SMEM_BYTES, st>>>(ma, mb, a);
-        e = cudaGetLastError();
-    }
+    const int grid = std::min(a.tiles, g_sms > 0 ? g_sms : 152);
+    if (P.df32) tc_terms_kernel<true><<<grid, THREADS, SMEM_BYTES, st>>>(ma, mb, a);
+    else tc_terms_kernel<false><<<grid, THREADS, SMEM_BYTES, st>>>(ma, mb, a);
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) { why = std::string("tc_terms launch: ") + cudaGetErrorString(e); return OOC_ERR_CUDA; }
     return OOC_OK;
 }

@@ -137,26 +137,6 @@ def test_forms_k_zero(ooc, form):
 
 
 @pytest.mark.parametrize("form", [3, 2])
-def test_forms_on_cta_pairs(ooc, form):
-    """The CTA-pair (tcgen05 cta_group::2) tiles give the same accuracy; the ragged
-    last pair tile (rows past M) and a B half-tile per CTA are exercised."""
-    fp32 = form == 3
-    dt = torch.float32 if fp32 else torch.float64
-    M, N, K = 300, 200, 700
-    A = pinned_from(81, 0, M, K, synth.UNIFORM if fp32 else synth.LOGSPREAD, dtype=dt)
-    B = pinned_from(81, 1, K, N, synth.UNIFORM if fp32 else synth.LOGSPREAD, dtype=dt)
-    C = pinned_from(81, 2, M, N, synth.UNIFORM if fp32 else synth.LOGSPREAD, dtype=dt)
-    C0 = np64(C)
-    f = ooc.ooc_sgemm if fp32 else ooc.ooc_dgemm
-    rc = f("N", "N", M, N, K, 1.5, A, K, B, N, 0.5, C, N, 1 << 30, ooc.make_opts(form=form, flags=ooc.OOC_TC_PAIR),
-           None)
-    assert rc == 0, ooc.ooc_last_error()
-    ref = oracle.gemm("N", "N", 1.5, np64(A), np64(B), 0.5, C0)
-    assert oracle.rel_fro(np64(C), ref) <= (TOL_BF16X3 if fp32 else TOL_OZAKI)
-    _elementwise(ooc, form, np64(C), ref, A, B, "N", "N", 1.5, 0.5, C0)
-
-
-@pytest.mark.parametrize("form", [3, 2])
 def test_forms_with_k_chunks(ooc, form):
     """K streamed in chunks (the last one ragged): each chunk is split on its own and the partial
     results accumulate in C (FP32 for BF16x3, FP64 for Ozaki)."""
