@@ -186,6 +186,33 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+def fp64_peak(P, local, no_clocks):
+    """The device's FP64 peak measured by the library's probe (mma.sync f64 from registers,
+    the instruction the FP64 tile kernel runs), with the SM clock sampled while it runs:
+    (TFLOP/s, median SM MHz or None)."""
+    clk = ClockSampler(local, enabled=not no_clocks)
+    tf = P.ooc_query_fp64_peak(1.5)
+    c = clk.stop()
+    return tf, (c or {}).get("sm_mhz")
+
+
+def fp64_roof_fields(pk, pk_src, probe, achieved, run_mhz):
+    """Roofline fields of an FP64 kernel: the measured probe peak as the denominator, the bf16-derived
+    figure beside it as context, and the fraction normalised by the SM clocks of both measurements."""
+    tf, probe_mhz = probe
+    derived = pk["bf16_tflops_sustained"] * NOMINAL_FP64_TF / NOMINAL_BF16_TF
+    out = {"peak": tf, "frac": achieved / tf if achieved and tf else None,
+           "peak_source": "measured: FP64 mma.sync probe (ooc_query_fp64_peak) in this run at %s MHz" % (
+               "%.0f" % probe_mhz if probe_mhz else "unsampled"),
+           "peak_derived_tflops": derived,
+           "peak_derived_source": "%s bf16 sustained %.1f TF x nominal FP64/BF16 ratio %.2f/%.0f" % (
+               pk_src, pk["bf16_tflops_sustained"], NOMINAL_FP64_TF, NOMINAL_BF16_TF),
+           "probe_sm_mhz": probe_mhz, "run_sm_mhz": run_mhz}
+    if achieved and tf and probe_mhz and run_mhz:
+        out["frac_clock_normalised"] = (achieved / run_mhz) / (tf / probe_mhz)
+    return out
+
+
 def sample_blocks(w, count, r, seed=12345):
     rng = np.random.default_rng(seed)
     i0 = rng.integers(0, max(1, w["M"] - r + 1), size=count)
@@ -393,6 +420,7 @@ def run_ours(args, w, world, rank, local, pg):
     torch.cuda.synchronize()
     cublas_tf = 3 * 2 * 4096 ** 3 / (e0.elapsed_time(e1) / 1e3) / 1e12
     del a
+    probe = fp64_peak(P, local, args.no_clocks) if w["form"] == "fp64" else (None, None)
 
     clk = ClockSampler(local, enabled=not args.no_clocks)
     if pg:
@@ -422,17 +450,15 @@ def run_ours(args, w, world, rank, local, pg):
     tr = TRAFFIC.get(args.config)
     traffic = tr["bytes"] if tr and not args.n and (s0.mb, s0.nb, s0.kb) == tr["plan"] else None
     if w["form"] == "fp64":
-        peak = pk["bf16_tflops_sustained"] * NOMINAL_FP64_TF / NOMINAL_BF16_TF
         achieved = flops * n_steps / ker_s / 1e12
         roof = {"bound": "tensor", "kernel": "fp64_tile_kernel (FP64 mma.sync, TMA-fed)",
-                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                "achieved": achieved, "unit": "TFLOP/s", "traffic": traffic,
                 "traffic_alg_bytes": 8.0 * (s0.mb * s0.kb + s0.kb * s0.nb + 2 * s0.mb * s0.nb),
                 "traffic_source": tr["profile"] if traffic else None,
-                "peak_source": "%s bf16 sustained %.1f TF x nominal FP64/BF16 ratio %.2f/%.0f" % (
-                    pk_src, pk["bf16_tflops_sustained"], NOMINAL_FP64_TF, NOMINAL_BF16_TF),
                 "fp64_cublas_measured_tflops": cublas_tf, "frac_of_cublas_dgemm": achieved / cublas_tf,
                 "launches_per_step": s0.steps}
-        compute_peak = peak
+        roof.update(fp64_roof_fields(pk, pk_src, probe, achieved, (clocks or {}).get("sm_mhz")))
+        compute_peak = roof["peak"]
     else:
         peak = pk["bf16_tflops_sustained"]
         achieved = flops * s0.products * n_steps / ker_s / 1e12
@@ -573,6 +599,7 @@ def run_batched_bench(args, w, world, rank, local, pg):
                   "pass": max(errs) <= 1e-13}
         cpu = {"value": fl / t_or / 1e12, "unit": "TFLOP/s", "cores": used, "kind": "oracle",
                "sample": "one %dx%d block of C in each of %d problems, %.1f s" % (r, r, len(errs), t_or)}
+    probe = fp64_peak(P, local, args.no_clocks)
     clk = ClockSampler(local, enabled=not args.no_clocks)
     if pg:
         pg.barrier()
@@ -591,9 +618,11 @@ def run_batched_bench(args, w, world, rank, local, pg):
         return
     s0 = stats[0][0]
     pk, pk_src = peaks()
-    peak = pk["bf16_tflops_sustained"] * NOMINAL_FP64_TF / NOMINAL_BF16_TF
     # the two halves' kernels overlap, so the summed kernel time over-counts: device time instead
     achieved = flops * n_steps / dev_s / 1e12 if dev_s > 0 else None
+    roof = {"bound": "tensor", "kernel": "fp64_tile_kernel (FP64 mma.sync, TMA-fed)", "achieved": achieved,
+            "unit": "TFLOP/s", "traffic": None}
+    roof.update(fp64_roof_fields(pk, pk_src, probe, achieved, (clocks or {}).get("sm_mhz")))
     line = {
         "metric": "out-of-core GEMM effective TFLOP/s incl. transfers",
         "value": world * flops * n_steps / dev_s / 1e12, "unit": "TFLOP/s", "n_gpus": world,
@@ -607,10 +636,7 @@ def run_batched_bench(args, w, world, rank, local, pg):
                                    w["budget"] / 2 ** 30, " (CUDA graph)" if graph else ""),
                    "problems": len(shapes), "total_flop": flops, "planner": planner,
                    "l2": "inputs larger than L2 (tens of GiB of host operands per step)"},
-        "roofline": {"bound": "tensor", "kernel": "fp64_tile_kernel (FP64 mma.sync, TMA-fed)",
-                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak if achieved else None, "traffic": None,
-                     "peak_source": "%s bf16 sustained x nominal FP64/BF16 ratio" % pk_src},
+        "roofline": roof,
         "e2e": {"value": world * flops * n_steps / wall_s / 1e12, "unit": "TFLOP/s",
                 "h2d_bytes_per_step": s0.h2d_bytes, "d2h_bytes_per_step": s0.d2h_bytes},
         "gpu_launches": sum(st.kernel_launches for st, _ in stats),
@@ -853,6 +879,7 @@ def run_level3_bench(args, w, world, rank, local, pg):
     if rank == 0:
         parity, cpu = level3_parity(w, ops, snap, cores)
     level3_restore(w, ops)
+    probe = fp64_peak(P, local, args.no_clocks) if args.form != "ozaki" else (None, None)
     clk = ClockSampler(local, enabled=not args.no_clocks)
     if pg:
         pg.barrier()
@@ -874,21 +901,23 @@ def run_level3_bench(args, w, world, rank, local, pg):
     s0 = stats[0][0]
     value = world * flops * args.steps / wall_s / 1e12
     pk, pk_src = peaks()
-    compute_peak = (pk["bf16_tflops_sustained"] * NOMINAL_FP64_TF / NOMINAL_BF16_TF if args.form != "ozaki"
-                    else pk["bf16_tflops_sustained"] / 36.0)
-    t_roof = flops / (compute_peak * 1e12)
+    achieved = flops * args.steps / wall_s / 1e12
+    roof = {"bound": "tensor", "kernel": "pipelined out-of-core GEMM updates (%s tile kernel)" % (
+                "tc_terms Ozaki" if args.form == "ozaki" else "fp64_tile"),
+            "achieved": achieved, "unit": "TFLOP/s", "traffic": None}
+    if args.form != "ozaki":
+        roof.update(fp64_roof_fields(pk, pk_src, probe, achieved, (clocks or {}).get("sm_mhz")))
+    else:
+        nprod = s0.products or 45
+        roof.update({"peak": pk["bf16_tflops_sustained"] / nprod, "frac": achieved / (pk["bf16_tflops_sustained"] / nprod),
+                     "peak_source": "%s bf16 sustained %.1f TF / %d Ozaki digit products" % (
+                         pk_src, pk["bf16_tflops_sustained"], nprod)})
     line = {
         "metric": metric, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * wall_s / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Philox, pinned host)",
         "config": cfg,
-        "roofline": {"bound": "tensor", "kernel": "pipelined out-of-core GEMM updates (%s tile kernel)" % (
-                         "tc_terms Ozaki" if args.form == "ozaki" else "fp64_tile"),
-                     "achieved": flops * args.steps / wall_s / 1e12, "peak": compute_peak, "unit": "TFLOP/s",
-                     "frac": t_roof * args.steps / wall_s, "traffic": None,
-                     "peak_source": "%s bf16 sustained %.1f TF x %s" % (
-                         pk_src, pk["bf16_tflops_sustained"],
-                         "nominal FP64/BF16 ratio" if args.form != "ozaki" else "1/36 Ozaki products")},
+        "roofline": roof,
         "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": s0.h2d_bytes,
                 "d2h_bytes_per_step": s0.d2h_bytes},
         "gpu_launches": s0.kernel_launches,
@@ -1106,6 +1135,7 @@ def run_pipe_bench(args, w, world, rank, local, pg):
                   "pass": max(errs) <= 1e-13}
         cpu = {"value": 2.0 * r * r * K * len(blocks) / dt / 1e12, "unit": "TFLOP/s", "cores": used,
                "kind": "oracle", "sample": "%d seeded %dx%d blocks of C, K=%d, %.1f s" % (len(blocks), r, r, K, dt)}
+    probe = fp64_peak(P, local, args.no_clocks)
     clk = ClockSampler(local, enabled=not args.no_clocks)
     if pg:
         pg.barrier()
@@ -1123,17 +1153,16 @@ def run_pipe_bench(args, w, world, rank, local, pg):
         return
     s0 = runs[0][0]
     pk, pk_src = peaks()
-    peak = pk["bf16_tflops_sustained"] * NOMINAL_FP64_TF / NOMINAL_BF16_TF
     achieved = flops * args.steps / sum(s_.kernel_seconds for s_, _ in runs) / 1e12
+    roof = {"bound": "tensor", "kernel": "fp64_tile_kernel (FP64 mma.sync, TMA-fed)", "achieved": achieved,
+            "unit": "TFLOP/s", "traffic": None}
+    roof.update(fp64_roof_fields(pk, pk_src, probe, achieved, (clocks or {}).get("sm_mhz")))
     line = {
         "metric": "out-of-core GEMM effective TFLOP/s incl. transfers (pipeline-language schedule)",
         "value": world * flops * args.steps / dev / 1e12, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * dev / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Philox, pinned host)", "config": cfg,
-        "roofline": {"bound": "tensor", "kernel": "fp64_tile_kernel (FP64 mma.sync, TMA-fed)", "achieved": achieved,
-                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                     "peak_source": "%s bf16 sustained %.1f TF x nominal FP64/BF16 ratio" % (
-                         pk_src, pk["bf16_tflops_sustained"])},
+        "roofline": roof,
         "plan": {"mb": plan["mb"], "nb": plan["nb"], "kb": plan["kb"], "rings": rings},
         "native_same_plan": {"value": flops * len(nat) / sum(s_.device_seconds for s_, _ in nat) / 1e12,
                              "unit": "TFLOP/s", "h2d_bytes": nat[0][0].h2d_bytes, "d2h_bytes": nat[0][0].d2h_bytes},

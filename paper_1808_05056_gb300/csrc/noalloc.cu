@@ -129,6 +129,7 @@ extern "C" int ooc_dgemm_noalloc(char transA, char transB, int64_t M, int64_t N,
     rc = make_plan(rq, p, why);
     if (rc) return noalloc_fail(rc, why);
     if (p.device_bytes > kNoallocArenaBytes) return noalloc_fail(OOC_ERR_BUDGET, "plan exceeds the no-alloc arena");
+    p.b_prefetch = false;  // one stream: copies cannot run ahead of the kernels anyway
     std::vector<Op> ops;
     build_schedule(p, ops);
 

@@ -142,11 +142,13 @@ int encode_map_3d_bf16(void* map_out, const void* base, uint64_t inner, uint64_t
 // The Ozaki groups of the tensor-core kernel: digit products (s, t) with
 // s + t <= S + 1, two consecutive t per group so that the group loads the A
 // plane s once; each product's exact FP32 sum is weighted 2^(-beta (s + t)).
+// Groups sharing a pair of B planes run back to back (t outer, s inner): the
+// tiles in flight then re-read those B planes from L2 rather than DRAM.
 void ozaki_groups(TcProblem& P, int S)
 {
     int n = 0;
-    for (int s1 = 1; s1 <= S; ++s1)
-        for (int t1 = 1; t1 <= S + 1 - s1; t1 += 2) {
+    for (int t1 = 1; t1 <= S; t1 += 2)
+        for (int s1 = 1; s1 <= S + 1 - t1; ++s1) {
             TcGroupSpec& g = P.groups[n++];
             const bool two = t1 + 1 <= S + 1 - s1;
             g.na = 1; g.nb = two ? 2 : 1; g.np = two ? 2 : 1;
@@ -565,6 +567,12 @@ int issue_ops(Exec& x, const Plan& p, const std::vector<Op>& ops, const Operands
                 src = hC + (t.r * p.mb * o.ldc + t.c * p.nb) * es;
                 rows = p.rows_of(t.r); width = p.cols_of(t.c);
                 spitch = o.ldc * es; dpitch = p.ldc_dev * es;
+            }
+            if (op.nparts > 1) {  // one row range of the chunk (B prefetch pieces)
+                const int64_t r0 = rows * op.part / op.nparts, r1 = rows * (op.part + 1) / op.nparts;
+                src += r0 * spitch;
+                dst += r0 * dpitch;
+                rows = r1 - r0;
             }
             if (rows > 0 && width > 0) {
                 if (spitch == width * es && dpitch == width * es)

@@ -51,6 +51,9 @@ struct Plan {
     // (which accumulate onto the partial sums instead of applying beta).
     int32_t nR = 0;
     int32_t session_step = -1;
+    // Whole-K B slices of the next block column are copied ahead, in row ranges
+    // between the A loads of the current column (schedule generator, plan.cpp)
+    bool b_prefetch = true;
 
     int64_t rows_of(int64_t i) const { return (i + 1) * mb <= M ? mb : M - i * mb; }
     int64_t cols_of(int64_t j) const { return (j + 1) * nb <= N ? nb : N - j * nb; }
@@ -127,6 +130,7 @@ struct Op {
     bool first = false, last = false;
     int32_t kernel = -1;           // pipeline-language kernels: which built-in
     int32_t mode = 0;              // and how its output tile starts (pipe.cpp)
+    int32_t part = 0, nparts = 1;  // H2D: rows [part, part + 1) * rows / nparts of the operand chunk
 };
 
 // Events: ready(s) after a load into slot s, free(s) after a kernel read s,

@@ -21,6 +21,7 @@
 // the event recorded after the slot's last reader, and records a ready event
 // that the compute stream waits on.  H2D, compute and D2H each have a stream.
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 #include <cstring>
 #include <limits>
@@ -309,6 +310,8 @@ int make_plan(const PlanRequest& rq, Plan& p, std::string& why)
     p.tri = rq.tri; p.tri_off = rq.tri_off;
     p.nR = rq.nR; p.session_step = rq.session_step;
     p.lda_host = rq.lda; p.ldb_host = rq.ldb; p.ldc_host = rq.ldc;
+    // OOC_B_PREFETCH=0 issues each B slice at its column switch (the schedule without the prefetch)
+    if (const char* e = std::getenv("OOC_B_PREFETCH")) p.b_prefetch = std::atoi(e) != 0;
     int form = rq.opts.form;
     if (form == OOC_FORM_AUTO) form = (rq.es == 8) ? OOC_FORM_FP64 : OOC_FORM_BF16X3;
     if (rq.es == 8 && form != OOC_FORM_FP64 && form != OOC_FORM_OZAKI) {
@@ -625,12 +628,57 @@ struct Gen {
         return victim;
     }
 
+    // Piece `part` of the next column's whole-K B slice (B prefetch): the first
+    // piece takes the least recently used B slot, after its last readers.
+    int pf_slot = -1;
+    void prefetch_piece(const Tag& tg, int part, int nparts, int64_t t, int64_t jn)
+    {
+        const int lo = p.nA, n = p.nB;
+        if (part == 0) {
+            int victim = -1;
+            for (int s = lo; s < lo + n; ++s)
+                if (content[s].m < 0) { victim = s; break; }
+            if (victim < 0) {
+                victim = lo;
+                for (int s = lo + 1; s < lo + n; ++s)
+                    if (last_use[s] < last_use[victim]) victim = s;
+            }
+            if (read_since_load[victim]) emit_wait(kStreamH2D, ev_free(p, victim));
+            pf_slot = victim;
+            content[victim] = tg;
+            last_use[victim] = t;
+            read_since_load[victim] = false;
+            compute_synced[victim] = false;
+        }
+        Op o; o.kind = kH2D; o.stream = kStreamH2D; o.wslot = pf_slot; o.wtag = tg;
+        o.i = 0; o.j = jn; o.kc = 0; o.part = part; o.nparts = nparts;
+        push(o);
+        emit_record(kStreamH2D, ev_ready(p, pf_slot));
+    }
+
+    int64_t updated_blocks(int64_t j) const
+    {
+        int64_t n = 0;
+        for (int64_t i = 0; i < p.h; ++i) n += p.block_class(i, j) != 0;
+        return n;
+    }
+
     void run()
     {
         const int a0 = 0, b0 = p.nA, c0 = p.nA + p.nB;
         const bool have_k = p.K > 0;
         int64_t nblk = 0;  // blocks issued so far: C blocks take the C slots in turn
-        for (int64_t j = 0; j < p.w; ++j)
+        constexpr int kMaxPieces = 8;
+        for (int64_t j = 0; j < p.w; ++j) {
+            // B prefetch: with whole-K B slices and a spare B slot, the next column's slice is
+            // copied in row ranges after the A loads of this column's 2nd, 3rd, ... updated blocks,
+            // so the column switch finds it resident instead of waiting for the whole slice
+            const int64_t ublk = updated_blocks(j);
+            const int npieces = (p.b_prefetch && have_k && p.nkc == 1 && p.nB >= 2 && j + 1 < p.w && ublk >= 2 &&
+                                 updated_blocks(j + 1) > 0)
+                                    ? (int)std::min<int64_t>(kMaxPieces, ublk - 1)
+                                    : 0;
+            int64_t u = 0;  // updated blocks of this column so far
             for (int64_t i = 0; i < p.h; ++i) {
                 const int cls = p.block_class(i, j);
                 if (cls == 0) continue;  // no element of this block is updated
@@ -649,6 +697,7 @@ struct Gen {
                     if (have_k) {
                         sa = ensure(kMatA, Tag{kMatA, i, kc, 0}, t, a0, p.nA, i, j, kc);
                         sb = ensure(kMatB, Tag{kMatB, kc, j, 0}, t, b0, p.nB, i, j, kc);
+                        if (u >= 1 && u <= npieces) prefetch_piece(Tag{kMatB, 0, j + 1, 0}, (int)(u - 1), npieces, t, j + 1);
                     }
                     if (kc == 0) {
                         const Tag ct{kMatC, i, j, 0};
@@ -702,7 +751,9 @@ struct Gen {
                         d2h_pending[sc] = true;
                     }
                 }
+                ++u;
             }
+        }
     }
 };
 

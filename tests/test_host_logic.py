@@ -206,7 +206,38 @@ CASES = [
     (256, 256, 512, 8, 1, 0, dict(mb=64, nb=128, kb=128, depth=2, c_buffers=2)),
     (200, 130, 0, 8, 1, 1 << 20, {}),
     (640, 64, 640, 8, 1, 0, dict(mb=64, nb=64, kb=640, depth=2, c_buffers=2)),
+    # whole-K B slices, two B slots, several blocks per column: the next column's B slice is
+    # prefetched in row ranges between this column's A loads
+    (1000, 700, 300, 8, 1, 0, dict(mb=128, nb=128, kb=300, depth=2, c_buffers=2, b_buffers=2)),
+    (1024, 1024, 512, 4, 1, 0, dict(form=3, mb=256, nb=256, depth=3, b_buffers=2)),
 ]
+
+
+def test_next_b_slice_is_prefetched_in_pieces_before_the_column_switch():
+    """Whole-K B slices with a spare B slot: the next column's slice is copied as row-range pieces
+    issued between the current column's kernels, all of them before the next column's first
+    kernel, and the first of them after the current column's second A load (so it never waits
+    for the kernel issued just before it)."""
+    M, N, K = 1000, 700, 300
+    opts = P.make_opts(mb=128, nb=128, kb=300, depth=2, c_buffers=2, b_buffers=2)
+    plan = P.ooc_plan(M, N, K, 8, 1, 1 << 40, opts)
+    assert plan["kb"] == K and plan["b_buffers"] == 2
+    ops = P.ooc_schedule(M, N, K, 8, 1, 1 << 40, opts)
+    h, w = -(-M // 128), -(-N // 128)
+    kernel_pos = {}
+    b_writes = {}
+    for n, o in enumerate(ops):
+        if o["kind"] == 1:
+            kernel_pos.setdefault(o["write_tag"][2], []).append(n)
+        elif o["kind"] == 0 and o["write_tag"][0] == 1:
+            b_writes.setdefault(o["write_tag"][2], []).append(n)
+    assert len(b_writes[0]) == 1                       # the first column's slice: one copy
+    for j in range(1, w):
+        pieces = b_writes[j]
+        assert len(pieces) == min(8, h - 1)            # the others: pieces
+        assert max(pieces) < kernel_pos[j][0]          # all before the column's first kernel
+        assert min(pieces) > kernel_pos[j - 1][0]      # the first after the previous column's first kernel
+        assert min(pieces) < kernel_pos[j - 1][-1]     # issued while that column still runs
 
 
 @pytest.mark.parametrize("case", range(len(CASES)))
