@@ -141,15 +141,23 @@ typedef struct {
     int64_t ldc;
 } ooc_gemm_desc;
 
-#define OOC_BATCH_GRAPH 2u  /* capture the whole batched pipeline as one CUDA graph, then launch it */
+#define OOC_BATCH_GRAPH 2u     /* capture the whole batched pipeline as one CUDA graph, then launch it */
+#define OOC_BATCH_STREAMED 16u /* run every batched problem through its own out-of-core pipeline */
 
 /*
  * A stream of uneven out-of-core DGEMMs in one call (each one the Section IV
  * problem on its own operands; problems must not share output memory).  The
- * device budget is split into two halves: consecutive problems alternate
- * halves and compute streams, so the copies and kernels of problem g + 1
- * overlap problem g, while problem g + 2 waits for problem g to finish.  Each
- * problem is planned for half the budget with opts (form: FP64 or Ozaki).
+ * device budget is split into two halves.  FP64 batches whose problems each
+ * fit whole in half the budget (A, B and C, rows padded to an even length)
+ * run grouped, unless OOC_BATCH_STREAMED is set: consecutive problems with
+ * the same transposes are packed into one half (at most 64 per group), copied
+ * in with one copy per operand, multiplied by one persistent launch over all
+ * their tiles and copied out, groups alternating halves so that one group's
+ * copies overlap the other's kernel; stats->steps then counts groups and
+ * stats->blocks problems.  Otherwise consecutive problems alternate halves
+ * and compute streams, so the copies and kernels of problem g + 1 overlap
+ * problem g, while problem g + 2 waits for problem g to finish; each problem
+ * is planned for half the budget with opts (form: FP64 or Ozaki).
  * With OOC_BATCH_GRAPH in opts->flags the issued copies, kernels and events
  * are captured into one CUDA graph and launched as a single graph.  stats
  * (nullable) receives totals: seconds, device_seconds, kernel_seconds (0 in

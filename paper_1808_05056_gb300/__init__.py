@@ -67,6 +67,7 @@ class ooc_gemm_desc(ctypes.Structure):
 
 
 OOC_BATCH_GRAPH = 2
+OOC_BATCH_STREAMED = 16
 OOC_PLAN_MODEL = 4
 OOC_MLP_INPUTS = 16
 OOC_MLP_PARAMS = 5313

@@ -313,6 +313,211 @@ int launch_variant(const CUtensorMap& ma, const CUtensorMap& mb, const Fp64Args&
     return OOC_OK;
 }
 
+// ---------------------------------------------------------------- grouped --
+// One launch over the tiles of up to kGroupMax independent problems whose
+// operands are all resident (a batch of uneven GEMMs): the CTAs walk the
+// concatenated list of (problem, tile) items -- each problem's tiles in the
+// raster order of tile_of -- with the stage ring running on across items and
+// problems, so one launch's tail and pipeline fill are paid once per group of
+// problems instead of once per problem.  Each problem's tensor maps live in
+// the kernel parameters (no device-side descriptor copy, so the launch can be
+// captured in a CUDA graph).
+struct GroupProb {
+    CUtensorMap ma, mb;
+    double* C;
+    int64_t ldc, M, N, K;
+    int64_t tiles_n, tile_begin;  // tiles per row of tiles; first item of this problem
+    double alpha, beta;
+    int read_c, pad;
+};
+
+struct GroupArgs {
+    int count;
+    int64_t tiles;  // items in all problems
+    int* err;
+    GroupProb p[kGroupMax];
+};
+
+// the problem holding item t (tile_begin ascending, first entry 0)
+__device__ __forceinline__ int group_problem(const GroupArgs& g, int64_t t)
+{
+    int lo = 0, hi = g.count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (g.p[mid].tile_begin <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void group_tile(const GroupProb& q, int64_t t, int64_t& tm, int64_t& tn)
+{
+    const int64_t local = t - q.tile_begin;
+    const int64_t tiles_m = (q.M + BM - 1) / BM;
+    const int64_t per_group = kRasterRows * q.tiles_n;
+    const int64_t gr = local / per_group, r = local % per_group;
+    const int64_t first = gr * kRasterRows;
+    const int64_t rows = tiles_m - first < kRasterRows ? tiles_m - first : kRasterRows;
+    tm = first + r % rows;
+    tn = r / rows;
+}
+
+template <bool A_KMAJOR, bool B_KMAJOR>
+__global__ void __launch_bounds__(THREADS) fp64_group_kernel(const __grid_constant__ GroupArgs g)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    double* stages = reinterpret_cast<double*>(base);
+    uint64_t* full = reinterpret_cast<uint64_t*>(base + STAGES * STAGE_BYTES);
+    uint64_t* empty = full + STAGES;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], CONSUMER_WARPS);
+        }
+        mbar_fence_init();
+    }
+    __syncthreads();
+
+    if (warp == CONSUMER_WARPS) {
+        // ---------------- producer ----------------
+        if (lane != 0) return;
+        int64_t it = 0;  // stages issued so far (ring position)
+        bool ok = true;
+        for (int64_t t = blockIdx.x; t < g.tiles && ok; t += gridDim.x) {
+            const GroupProb& q = g.p[group_problem(g, t)];
+            int64_t tm64, tn64;
+            group_tile(q, t, tm64, tn64);
+            const int32_t tm = (int32_t)tm64, tn = (int32_t)tn64;
+            const int64_t nk = (q.K + BK - 1) / BK;
+            for (int64_t ks = 0; ks < nk; ++ks, ++it) {
+                const int s = (int)(it % STAGES);
+                if (!mbar_wait(&empty[s], (uint32_t)((it / STAGES) & 1) ^ 1u, g.err, kErrWaitEmpty)) {
+                    ok = false;
+                    break;
+                }
+                double* sA = stages + (size_t)s * (STAGE_A + STAGE_B);
+                double* sB = sA + STAGE_A;
+                mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+                const int32_t k0 = (int32_t)(ks * BK);
+                if (A_KMAJOR) tma_load_2d(sA, &q.ma, &full[s], k0, tm * BM);
+                else tma_load_2d(sA, &q.ma, &full[s], tm * BM, k0);
+                if (B_KMAJOR) tma_load_2d(sB, &q.mb, &full[s], k0, tn * BN);
+                else tma_load_2d(sB, &q.mb, &full[s], tn * BN, k0);
+            }
+        }
+        if (!ok) {
+            // let the copies already issued land before the CTA exits
+            for (int64_t w = (it > STAGES ? it - STAGES : 0); w < it; ++w) {
+                const int s = (int)(w % STAGES);
+                const uint64_t t0 = globaltimer_ns();
+                while (!mbar_try_wait(smem_u32(&full[s]), (uint32_t)((w / STAGES) & 1)) &&
+                       globaltimer_ns() - t0 < kWaitLimitNs) {
+                }
+            }
+        }
+        return;
+    }
+
+    // ---------------- consumers ----------------
+    const int wm = warp >> 1, wn = warp & 1;
+    const int fr = lane >> 2, fc = lane & 3;
+    double acc[4][4][2];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b][0] = acc[a][b][1] = 0.0;
+    int64_t it = 0;
+    for (int64_t t = blockIdx.x; t < g.tiles; t += gridDim.x) {
+        const GroupProb& q = g.p[group_problem(g, t)];
+        const int64_t nk = (q.K + BK - 1) / BK;
+        for (int64_t ks = 0; ks < nk; ++ks, ++it) {
+            const int s = (int)(it % STAGES);
+            if (!mbar_wait(&full[s], (uint32_t)((it / STAGES) & 1), g.err, kErrWaitFull)) return;
+            const double* sA = stages + (size_t)s * (STAGE_A + STAGE_B);
+            const double* sB = sA + STAGE_A;
+#pragma unroll
+            for (int kk = 0; kk < BK; kk += 4) {
+                double af[4], bf[4];
+#pragma unroll
+                for (int mi = 0; mi < 4; ++mi) {
+                    const int r = wm * 32 + mi * 8 + fr, k = kk + fc;
+                    af[mi] = A_KMAJOR ? sA[r * BK + k] : sA[k * BM + r];
+                }
+#pragma unroll
+                for (int ni = 0; ni < 4; ++ni) {
+                    const int n = wn * 32 + ni * 8 + fr, k = kk + fc;
+                    bf[ni] = B_KMAJOR ? sB[n * BK + k] : sB[k * BN + n];
+                }
+#pragma unroll
+                for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+                    for (int ni = 0; ni < 4; ++ni) dmma_8x8x4(acc[mi][ni][0], acc[mi][ni][1], af[mi], bf[ni]);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);
+        }
+        // epilogue of item t: C = alpha acc + beta C (K == 0: beta C)
+        int64_t tm, tn;
+        group_tile(q, t, tm, tn);
+#pragma unroll
+        for (int mi = 0; mi < 4; ++mi) {
+            const int64_t row = tm * BM + wm * 32 + mi * 8 + fr;
+#pragma unroll
+            for (int ni = 0; ni < 4; ++ni) {
+                const int64_t col = tn * BN + wn * 32 + ni * 8 + fc * 2;
+                if (row < q.M) {
+                    double* c = q.C + row * q.ldc + col;
+                    if (col + 1 < q.N) {
+                        double2 v;
+                        v.x = q.alpha * acc[mi][ni][0];
+                        v.y = q.alpha * acc[mi][ni][1];
+                        if (q.read_c) {
+                            const double2 o = *reinterpret_cast<const double2*>(c);
+                            v.x += q.beta * o.x;
+                            v.y += q.beta * o.y;
+                        }
+                        *reinterpret_cast<double2*>(c) = v;
+                    } else if (col < q.N) {
+                        double v = q.alpha * acc[mi][ni][0];
+                        if (q.read_c) v += q.beta * c[0];
+                        c[0] = v;
+                    }
+                }
+                acc[mi][ni][0] = acc[mi][ni][1] = 0.0;
+            }
+        }
+    }
+}
+
+template <bool AK, bool BKM>
+int launch_group_variant(const GroupArgs& a, cudaStream_t st, std::string& why)
+{
+    static int occ = 0, sms = 0;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaFuncSetAttribute(fp64_group_kernel<AK, BKM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)SMEM_BYTES);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fp64_group_kernel<AK, BKM>, THREADS, SMEM_BYTES);
+        sms = device_sm_count();
+    });
+    if (occ <= 0) {
+        why = "fp64 group kernel cannot be resident (occupancy 0)";
+        return OOC_ERR_CUDA;
+    }
+    const int64_t grid = std::min<int64_t>(a.tiles > 0 ? a.tiles : 1, (int64_t)occ * sms);
+    fp64_group_kernel<AK, BKM><<<(unsigned)grid, THREADS, SMEM_BYTES, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        why = std::string("fp64 group launch: ") + cudaGetErrorString(e);
+        return OOC_ERR_CUDA;
+    }
+    return OOC_OK;
+}
+
 }  // namespace
 
 int launch_fp64_tile(bool a_kmajor, bool b_kmajor, int64_t M, int64_t N, int64_t K, double alpha,
@@ -350,6 +555,51 @@ int launch_fp64_tile(bool a_kmajor, bool b_kmajor, int64_t M, int64_t N, int64_t
     if (a_kmajor && !b_kmajor) return launch_variant<true, false>(ma, mbm, a, st, why);
     if (!a_kmajor && b_kmajor) return launch_variant<false, true>(ma, mbm, a, st, why);
     return launch_variant<false, false>(ma, mbm, a, st, why);
+}
+
+int launch_fp64_group(bool a_kmajor, bool b_kmajor, const Fp64GroupSpec* probs, int count, int* err, void* stream,
+                      std::string& why, int64_t* tiles_out)
+{
+    if (count <= 0 || count > kGroupMax) {
+        why = "grouped launch: problem count outside 1.." + std::to_string(kGroupMax);
+        return OOC_ERR_INVALID_ARG;
+    }
+    static GroupArgs a;  // 24 KB of kernel parameters: not on the stack
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lk(mu);
+    std::memset(&a, 0, sizeof(a));
+    a.err = err;
+    int n = 0;
+    int64_t tiles = 0;
+    for (int i = 0; i < count; ++i) {
+        const Fp64GroupSpec& s = probs[i];
+        if (s.M <= 0 || s.N <= 0) continue;
+        GroupProb& q = a.p[n];
+        if (s.K > 0) {
+            int rc = a_kmajor ? encode_map_2d(&q.ma, 0, s.A, (uint64_t)s.K, (uint64_t)s.M, (uint64_t)s.lda, BK, BM, 0, why)
+                              : encode_map_2d(&q.ma, 0, s.A, (uint64_t)s.M, (uint64_t)s.K, (uint64_t)s.lda, BM, BK, 0, why);
+            if (rc != OOC_OK) return rc;
+            rc = b_kmajor ? encode_map_2d(&q.mb, 0, s.B, (uint64_t)s.K, (uint64_t)s.N, (uint64_t)s.ldb, BK, BN, 0, why)
+                          : encode_map_2d(&q.mb, 0, s.B, (uint64_t)s.N, (uint64_t)s.K, (uint64_t)s.ldb, BN, BK, 0, why);
+            if (rc != OOC_OK) return rc;
+        }
+        q.C = s.C; q.ldc = s.ldc;
+        q.M = s.M; q.N = s.N; q.K = s.K;
+        q.tiles_n = (s.N + BN - 1) / BN;
+        q.tile_begin = tiles;
+        q.alpha = s.alpha; q.beta = s.beta; q.read_c = s.read_c ? 1 : 0;
+        tiles += ((s.M + BM - 1) / BM) * q.tiles_n;
+        ++n;
+    }
+    if (tiles_out) *tiles_out = tiles;
+    if (n == 0) return OOC_OK;
+    a.count = n;
+    a.tiles = tiles;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (a_kmajor && b_kmajor) return launch_group_variant<true, true>(a, st, why);
+    if (a_kmajor && !b_kmajor) return launch_group_variant<true, false>(a, st, why);
+    if (!a_kmajor && b_kmajor) return launch_group_variant<false, true>(a, st, why);
+    return launch_group_variant<false, false>(a, st, why);
 }
 
 }  // namespace ooc

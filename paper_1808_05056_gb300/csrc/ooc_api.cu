@@ -778,6 +778,258 @@ int run_gemm_host(char ta, char tb, int64_t M, int64_t N, int64_t K, double alph
 
 namespace {
 
+// ------------------------------------------------------------- grouped batch --
+// Batched calls whose problems each fit in half of the budget: consecutive
+// problems are packed whole into one arena half as a group (at most kGroupMax,
+// one transpose pair), copied in with one copy per operand, multiplied by one
+// persistent grouped launch over all their tiles, and copied out; groups
+// alternate halves, each half on its own H2D / compute / D2H streams, so one
+// group's copies overlap the other half's kernel.  Compared with one
+// out-of-core pipeline per problem this pays a launch's tail and a pipeline
+// fill once per group instead of once per problem (Section IV's pipeline with
+// the group as its unit of work).
+namespace {
+
+struct DevMat {
+    size_t off = 0;   // byte offset in the half
+    int64_t ld = 0;   // device leading dimension (elements, even: TMA row pitch)
+};
+
+size_t mat_bytes(int64_t rows, int64_t ld) { return ((size_t)std::max<int64_t>(rows, 1) * ld * 8 + 255) / 256 * 256; }
+int64_t even(int64_t x) { return std::max<int64_t>(2, (x + 1) / 2 * 2); }
+
+// device bytes of problem d placed whole (A, B, C)
+size_t whole_bytes(const ooc_gemm_desc& d)
+{
+    const bool ta = d.transA == 'T' || d.transA == 't', tb = d.transB == 'T' || d.transB == 't';
+    const int64_t ar = ta ? d.K : d.M, ac = ta ? d.M : d.K, br = tb ? d.N : d.K, bc = tb ? d.K : d.N;
+    return mat_bytes(ar, even(ac)) + mat_bytes(br, even(bc)) + mat_bytes(d.M, even(d.N));
+}
+
+int copy_h2d(char* dst, int64_t dld, const void* src, int64_t sld, int64_t rows, int64_t cols, cudaStream_t s,
+             double& bytes)
+{
+    if (rows <= 0 || cols <= 0) return OOC_OK;
+    cudaError_t e;
+    if (sld == cols && dld == cols) e = cudaMemcpyAsync(dst, src, (size_t)rows * cols * 8, cudaMemcpyHostToDevice, s);
+    else e = cudaMemcpy2DAsync(dst, dld * 8, src, sld * 8, cols * 8, rows, cudaMemcpyHostToDevice, s);
+    bytes += (double)rows * cols * 8;
+    return e == cudaSuccess ? OOC_OK : OOC_ERR_CUDA;
+}
+
+}  // namespace
+
+int run_batched_grouped(int32_t count, const ooc_gemm_desc* d, size_t half, const ooc_opts& opts, bool use_graph,
+                        ooc_stats* stats, std::chrono::steady_clock::time_point t_host0)
+{
+    std::string why;
+    // groups: consecutive problems, same transposes, whole in one half, at most kGroupMax
+    struct Group {
+        int first = 0, n = 0;
+        bool ta = false, tb = false;
+    };
+    std::vector<Group> groups;
+    {
+        size_t used = 0;
+        for (int g = 0; g < count; ++g) {
+            if (d[g].M == 0 || d[g].N == 0) continue;
+            const bool ta = is_t(d[g].transA), tb = is_t(d[g].transB);
+            const size_t b = whole_bytes(d[g]);
+            if (groups.empty() || groups.back().ta != ta || groups.back().tb != tb || groups.back().n >= kGroupMax ||
+                used + b > half) {
+                groups.push_back(Group{g, 0, ta, tb});
+                used = 0;
+            }
+            groups.back().n = g - groups.back().first + 1;
+            used += b;
+        }
+    }
+    double flops = 0;
+    for (int g = 0; g < count; ++g) flops += 2.0 * (double)d[g].M * d[g].N * d[g].K;
+
+    Inject inj;
+    char* arena = nullptr;
+    bool own = false;
+    if (opts.workspace) {
+        if (opts.workspace_bytes < 2 * half + 256) return fail(OOC_ERR_INVALID_ARG, "workspace smaller than the budget");
+        arena = static_cast<char*>(opts.workspace);
+    } else {
+        if (inj.alloc) return fail(OOC_ERR_INJECTED, "injected arena allocation failure");
+        if (cudaMalloc(&arena, 2 * half + 256) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(OOC_ERR_ALLOC, "device arena of " + std::to_string(2 * half + 256) + " bytes");
+        }
+        own = true;
+    }
+    // resources, released on every return path
+    struct Res {
+        cudaStream_t s[7] = {};  // [0] fork/join, then per half: H2D, compute, D2H
+        cudaEvent_t ev[7] = {};  // per half: in, done, out; [6] fork
+        cudaEvent_t t0 = nullptr, t1 = nullptr;
+        std::vector<cudaEvent_t> kev;
+        char* arena = nullptr;
+        bool own = false;
+        void release()
+        {
+            for (auto& st : s)
+                if (st) cudaStreamSynchronize(st);
+            for (auto& st : s)
+                if (st) { cudaStreamDestroy(st); st = nullptr; }
+            for (auto& e : ev)
+                if (e) { cudaEventDestroy(e); e = nullptr; }
+            for (auto& e : kev)
+                if (e) cudaEventDestroy(e);
+            kev.clear();
+            if (t0) { cudaEventDestroy(t0); t0 = nullptr; }
+            if (t1) { cudaEventDestroy(t1); t1 = nullptr; }
+            if (own && arena) cudaFree(arena);
+            arena = nullptr;
+            cudaGetLastError();
+        }
+        ~Res() { release(); }
+    } r;
+    r.arena = arena;
+    r.own = own;
+    for (auto& st : r.s) CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    for (auto& e : r.ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    CK(cudaEventCreate(&r.t0));
+    CK(cudaEventCreate(&r.t1));
+    if (!use_graph) {
+        r.kev.resize(2 * groups.size(), nullptr);
+        for (auto& e : r.kev) CK(cudaEventCreate(&e));
+    }
+    int* err = reinterpret_cast<int*>(arena);
+    cudaStream_t s0 = r.s[0];
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    if (use_graph) CK(cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal));
+    else CK(cudaEventRecord(r.t0, s0));
+    CK(cudaMemsetAsync(err, 0, sizeof(int), s0));
+    CK(cudaEventRecord(r.ev[6], s0));
+    for (int k = 1; k < 7; ++k) CK(cudaStreamWaitEvent(r.s[k], r.ev[6], 0));
+    double h2d = 0, d2h = 0;
+    int launches = 0;
+    int rc = OOC_OK;
+    bool issued[2] = {false, false};
+    std::vector<Fp64GroupSpec> spec;
+    for (size_t G = 0; G < groups.size() && rc == OOC_OK; ++G) {
+        const Group& gr = groups[G];
+        const int h = (int)(G & 1);
+        char* base = arena + 256 + (size_t)h * half;
+        cudaStream_t sh = r.s[1 + 3 * h], sc = r.s[2 + 3 * h], sd = r.s[3 + 3 * h];
+        cudaEvent_t ev_in = r.ev[3 * h], ev_done = r.ev[3 * h + 1], ev_out = r.ev[3 * h + 2];
+        // the previous group of this half has copied its results out
+        if (issued[h]) CK(cudaStreamWaitEvent(sh, ev_out, 0));
+        spec.assign(gr.n, Fp64GroupSpec{});
+        size_t off = 0;
+        for (int q = 0; q < gr.n && rc == OOC_OK; ++q) {
+            const ooc_gemm_desc& p = d[gr.first + q];
+            Fp64GroupSpec& s = spec[q];
+            s.M = p.M; s.N = p.N; s.K = p.K;
+            s.alpha = p.alpha; s.beta = p.beta;
+            s.read_c = p.beta != 0.0;
+            if (p.M == 0 || p.N == 0) continue;
+            const int64_t ar = gr.ta ? p.K : p.M, ac = gr.ta ? p.M : p.K;
+            const int64_t br = gr.tb ? p.N : p.K, bc = gr.tb ? p.K : p.N;
+            s.lda = even(ac); s.ldb = even(bc); s.ldc = even(p.N);
+            char* dA = base + off;
+            off += mat_bytes(ar, s.lda);
+            char* dB = base + off;
+            off += mat_bytes(br, s.ldb);
+            char* dC = base + off;
+            off += mat_bytes(p.M, s.ldc);
+            s.A = reinterpret_cast<const double*>(dA);
+            s.B = reinterpret_cast<const double*>(dB);
+            s.C = reinterpret_cast<double*>(dC);
+            if (inj.copy >= 0 && (int64_t)(G * 3 + q) == inj.copy) { rc = fail(OOC_ERR_INJECTED, "injected copy failure"); break; }
+            if (p.K > 0) {
+                if (copy_h2d(dA, s.lda, p.A, p.lda, ar, ac, sh, h2d) || copy_h2d(dB, s.ldb, p.B, p.ldb, br, bc, sh, h2d)) {
+                    rc = fail(OOC_ERR_CUDA, "grouped batch: operand copy");
+                    break;
+                }
+            }
+            if (s.read_c && copy_h2d(dC, s.ldc, p.C, p.ldc, p.M, p.N, sh, h2d)) {
+                rc = fail(OOC_ERR_CUDA, "grouped batch: C copy");
+                break;
+            }
+        }
+        if (rc) break;
+        CK(cudaEventRecord(ev_in, sh));
+        CK(cudaStreamWaitEvent(sc, ev_in, 0));
+        if (inj.kernel >= 0 && (int64_t)G == inj.kernel) { rc = fail(OOC_ERR_INJECTED, "injected kernel failure"); break; }
+        if (!use_graph) CK(cudaEventRecord(r.kev[2 * G], sc));
+        rc = launch_fp64_group(!gr.ta, gr.tb, spec.data(), gr.n, err, sc, why);
+        if (rc) { rc = fail(rc, why); break; }
+        if (!use_graph) CK(cudaEventRecord(r.kev[2 * G + 1], sc));
+        ++launches;
+        CK(cudaEventRecord(ev_done, sc));
+        CK(cudaStreamWaitEvent(sd, ev_done, 0));
+        for (int q = 0; q < gr.n; ++q) {
+            const ooc_gemm_desc& p = d[gr.first + q];
+            const Fp64GroupSpec& s = spec[q];
+            if (p.M == 0 || p.N == 0) continue;
+            cudaError_t e;
+            if (p.ldc == p.N && s.ldc == p.N)
+                e = cudaMemcpyAsync(p.C, s.C, (size_t)p.M * p.N * 8, cudaMemcpyDeviceToHost, sd);
+            else
+                e = cudaMemcpy2DAsync(p.C, p.ldc * 8, s.C, s.ldc * 8, p.N * 8, p.M, cudaMemcpyDeviceToHost, sd);
+            if (e != cudaSuccess) { rc = fail(OOC_ERR_CUDA, "grouped batch: C copy out"); break; }
+            d2h += (double)p.M * p.N * 8;
+        }
+        CK(cudaEventRecord(ev_out, sd));
+        issued[h] = true;
+    }
+    // join every stream into s0
+    for (int k = 1; k < 7; ++k) {
+        CK(cudaEventRecord(r.ev[6], r.s[k]));
+        CK(cudaStreamWaitEvent(s0, r.ev[6], 0));
+    }
+    if (use_graph) {
+        CK(cudaStreamEndCapture(s0, &graph));
+        if (rc == OOC_OK) {
+            cudaError_t e = cudaGraphInstantiate(&gexec, graph, 0);
+            if (e == cudaSuccess) {
+                CK(cudaEventRecord(r.t0, s0));
+                e = cudaGraphLaunch(gexec, s0);
+            }
+            if (e != cudaSuccess) rc = fail(OOC_ERR_CUDA, std::string("grouped batch graph: ") + cudaGetErrorString(e));
+        }
+    }
+    CK(cudaEventRecord(r.t1, s0));
+    cudaError_t se = cudaStreamSynchronize(s0);
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (graph) cudaGraphDestroy(graph);
+    if (rc) return rc;
+    if (se != cudaSuccess) return fail(OOC_ERR_CUDA, std::string("grouped batch: ") + cudaGetErrorString(se));
+    int herr = 0;
+    CK(cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (herr != 0) return fail(OOC_ERR_TIMEOUT, "a device-side wait gave up (status " + std::to_string(herr) + ")");
+    if (stats) {
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, r.t0, r.t1));
+        stats->device_seconds = ms * 1e-3;
+        double ksum = 0;
+        for (size_t G = 0; !use_graph && G < groups.size(); ++G) {
+            CK(cudaEventElapsedTime(&ms, r.kev[2 * G], r.kev[2 * G + 1]));
+            ksum += ms;
+        }
+        stats->kernel_seconds = ksum * 1e-3;  // 0 in graph mode (not timed)
+        stats->h2d_bytes = h2d;
+        stats->d2h_bytes = d2h;
+        for (int g = 0; g < count; ++g) stats->blocks += d[g].M > 0 && d[g].N > 0;
+        stats->steps = (int64_t)groups.size();
+        stats->device_bytes = (int64_t)(2 * half + 256);
+        stats->form = OOC_FORM_FP64;
+        stats->kernel_launches = launches;
+    }
+    r.release();  // the arena free is part of the call's wall time
+    if (stats) {
+        stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_host0).count();
+        stats->tflops = stats->seconds > 0 ? flops / stats->seconds / 1e12 : 0.0;
+    }
+    return OOC_OK;
+}
+
 int run_batched(int32_t count, const ooc_gemm_desc* d, size_t budget, const ooc_opts* opts_in, ooc_stats* stats)
 {
     const auto t_host0 = std::chrono::steady_clock::now();
@@ -808,6 +1060,14 @@ int run_batched(int32_t count, const ooc_gemm_desc* d, size_t budget, const ooc_
     double hg = 0, dg = 0;
     const bool have_link = ooc_query_device(nullptr, &hg, &dg) == OOC_OK && hg > 0 && dg > 0;
     const size_t half = ((budget > 512 ? budget - 256 : 0) / 2) / 256 * 256;
+    // FP64 problems that each fit whole in half the budget: the grouped path (one persistent launch
+    // per group of problems) unless the caller asks for one out-of-core pipeline per problem
+    if ((opts.form == OOC_FORM_AUTO || opts.form == OOC_FORM_FP64) && !(opts.flags & OOC_BATCH_STREAMED)) {
+        bool all_fit = true;
+        for (int g = 0; g < count && all_fit; ++g)
+            if (d[g].M > 0 && d[g].N > 0) all_fit = whole_bytes(d[g]) <= half;
+        if (all_fit) return run_batched_grouped(count, d, half, opts, use_graph, stats, t_host0);
+    }
 
     // plans and schedules, each within half of the budget; the problems are planned in
     // parallel on host threads (planning is host work: candidate search, cost model)

@@ -208,6 +208,25 @@ int launch_fp64_tile(bool a_kmajor, bool b_kmajor, int64_t M, int64_t N, int64_t
                      bool read_c, double* C, int64_t ldc, int* err, void* stream,
                      std::string& why, int tri = 0, int64_t tri_off = 0);
 
+// Grouped FP64 tile GEMM: the problems' tiles in one persistent launch, each
+// problem's operands already on the device (conventions as launch_fp64_tile,
+// full updates only); at most kGroupMax problems.  *tiles_out (nullable)
+// receives the launch's work items.
+struct Fp64GroupSpec {
+    const double* A = nullptr;
+    int64_t lda = 0;
+    const double* B = nullptr;
+    int64_t ldb = 0;
+    double* C = nullptr;
+    int64_t ldc = 0;
+    int64_t M = 0, N = 0, K = 0;
+    double alpha = 1.0, beta = 0.0;
+    bool read_c = false;
+};
+constexpr int kGroupMax = 64;
+int launch_fp64_group(bool a_kmajor, bool b_kmajor, const Fp64GroupSpec* probs, int count, int* err, void* stream,
+                      std::string& why, int64_t* tiles_out = nullptr);
+
 // --- tensor-core split-product forms (tc_gemm.cu) -------------------------
 // A group: pairs (A plane, B plane) accumulated into one FP32 TMEM accumulator
 // and added into FP64 with weight 2^scale_exp after every K chunk.

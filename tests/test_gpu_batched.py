@@ -76,3 +76,43 @@ def test_batched_empty_and_errors(ooc):
     d.A = d.B = d.C = A.ctypes.data
     d.lda = d.ldb = d.ldc = 8
     assert ooc.ooc_dgemm_batched([d], 1 << 20) == ooc.OOC_ERR_NOT_PINNED
+
+
+@pytest.mark.parametrize("flags", [0, 2])
+def test_batched_grouped_path(ooc, flags):
+    """Every problem fits whole in half the budget: the grouped path (one persistent launch per
+    group of problems, whole-matrix copies), with and without CUDA-graph capture; all transpose
+    pairs (a group per change of pair), K = 0, beta = 0 with NaN in C, ragged tiles."""
+    probs = _problems(80)
+    for n in (1, 3):   # beta = 0 problems: C is never read
+        probs[n][9].fill_(float("nan"))
+    st = ooc.ooc_stats()
+    rc = ooc.ooc_dgemm_batched(_descs(ooc, probs), 256 << 20, ooc.make_opts(flags=flags), st)
+    assert rc == 0, ooc.ooc_last_error()
+    assert st.blocks == len(SHAPES)
+    assert 1 <= st.steps < len(SHAPES)          # groups, not problems
+    assert st.kernel_launches == st.steps
+    for ta, tb, M, N, K, al, be, A, B, C, C0 in probs:
+        ref = oracle.gemm(ta, tb, al, np64(A), np64(B), be, None if be == 0 else C0) if K else be * C0
+        assert oracle.rel_fro(np64(C), ref) <= 1e-13, (ta, tb, M, N, K)
+
+
+def test_batched_grouped_matches_streamed(ooc):
+    """The same batch through the grouped path and through one pipeline per problem."""
+    shapes = [("N", "N", 520 + 37 * q, 300 + 53 * q, 64 + 91 * q, 1.0, 0.5) for q in range(12)]
+    outs = []
+    for flags in (0, ooc.OOC_BATCH_STREAMED):
+        probs = []
+        for n, (ta, tb, M, N, K, al, be) in enumerate(shapes):
+            A = pinned_from(90 + n, 0, M, K, synth.INTEGER, 30)
+            B = pinned_from(90 + n, 1, K, N, synth.INTEGER, 30)
+            C = pinned_from(90 + n, 2, M, N, synth.INTEGER, 30)
+            probs.append((ta, tb, M, N, K, al, be, A, B, C, np64(C)))
+        st = ooc.ooc_stats()
+        rc = ooc.ooc_dgemm_batched(_descs(ooc, probs), 64 << 20, ooc.make_opts(flags=flags), st)
+        assert rc == 0, ooc.ooc_last_error()
+        outs.append([np64(p[9]) for p in probs])
+        for ta, tb, M, N, K, al, be, A, B, C, C0 in probs:
+            assert np.array_equal(np64(C), oracle.gemm(ta, tb, al, np64(A), np64(B), be, C0))  # integers: exact
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
