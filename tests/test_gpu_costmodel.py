@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 import synth
 from oracle import costmodel
 from gpu_util import pinned, pinned_from
@@ -76,8 +77,9 @@ def test_autotune_times_every_candidate(ooc):
     res = ooc.ooc_autotune(d, 8, 2 << 20, ooc.make_opts(form=ooc.OOC_FORM_FP64), max_candidates=6)
     assert 1 <= len(res) <= 6
     assert all(s > 0 for _, s in res)
-    # the last run left a correct product in C
-    np.testing.assert_allclose(C.numpy(), A.numpy() @ B.numpy(), rtol=1e-12, atol=1e-12)
+    # the last run left a correct product in C (element by element against the oracle)
+    ref = oracle.gemm("N", "N", 1.0, A.numpy().astype(np.float64), B.numpy().astype(np.float64), 0.0, None)
+    np.testing.assert_allclose(C.numpy(), ref, rtol=1e-12, atol=1e-12)
 
 
 def test_trained_model_gains_over_analytic_planner(ooc):
