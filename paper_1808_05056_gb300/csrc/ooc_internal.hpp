@@ -290,7 +290,9 @@ constexpr int kOzakiSlicesGemm = 8;
 constexpr int kOzakiSlicesFactor = 9;
 constexpr int kOzakiMaxSlices = 10;
 constexpr int kOzakiChunk = 4096;
-constexpr int kBf16x3Chunk = 128;
+// BF16x3: K between drains of the leading product's round-toward-zero FP32
+// accumulator (32 accumulations of up to one ulp each: 2^-18 of sum |x||y|)
+constexpr int kBf16x3Chunk = 512;
 
 int device_sm_count();
 void set_error(const std::string& msg);

@@ -7,10 +7,13 @@
 //   ll are below 2^-24 relative).  The tensor cores round their FP32
 //   accumulator toward zero, so each accumulator addition is biased by up to
 //   one ulp: the leading product hh has its own accumulator, drained every
-//   `chunk` of K (two K blocks, 8 additions) into an unbiased double-float
-//   (hi, lo) pair per output with TwoSum; the five small products, 2^-8 of
-//   hh and below, share a second accumulator that is drained far less often
-//   (every kSmallChunks chunks, 2048 of K) straight into lo.
+//   `chunk` of K (512: 32 additions) into an unbiased double-float (hi, lo)
+//   pair per output with TwoSum; the five small products, 2^-8 of hh and
+//   below, share a second accumulator drained every 2048 of K straight into
+//   lo.  The drains run on the epilogue warps, four of which share the MMA
+//   thread's sub-partition (TMEM lane quarters tie warps to sub-partitions):
+//   draining hh every 128 of K took enough of that thread's issue slots to
+//   cost a fifth of the tensor-core rate.
 //
 //   Ozaki (FP64-accurate, ooc_dgemm with OOC_FORM_OZAKI), after Ozaki, Ogita,
 //   Oishi and Rump's error-free splitting of matrix products: every row of A
@@ -32,7 +35,9 @@
 //   warps 2-17  epilogue: drain finished accumulators with tcgen05.ld into
 //               FP64 (Ozaki) or packed double-float FP32 (BF16x3) registers,
 //               32 columns of one row per thread, release them, and after the
-//               last chunk write alpha*acc*2^(e_i+f_j) + beta*C_old.
+//               last chunk write alpha*acc*2^(e_i+f_j) + beta*C_old, each store
+//               covering 8 rows x 4 consecutive columns (4 x 4 transposes by
+//               shuffles inside groups of 4 lanes).
 // TMEM: Ozaki uses two buffers of two 128-column accumulators (the group's two
 // products), so the tensor cores run the next group while the epilogue drains
 // the previous one; BF16x3 uses three buffers for hh and one accumulator for
@@ -41,7 +46,10 @@
 // The single issuing thread keeps its per-stage work to the MMAs themselves
 // (descriptor offsets precomputed per group, ring positions advanced without
 // division): at 64 cycles per 128 x 128 x 16 MMA, anything more starves the
-// tensor pipe.  CTA pairs (cta_group::2, 256 x 128 tiles with half of each B
+// tensor pipe.  For the same reason the ring releases whole stages: finer
+// slots (one 16 KiB plane tile each, with a wait and a release per tile) ran
+// at half the rate for both forms, even with the same shared-memory layout.
+// CTA pairs (cta_group::2, 256 x 128 tiles with half of each B
 // tile per CTA) were measured slower on GB300 for both forms (BF16x3 1216 vs
 // 1384, Ozaki 1337 vs 1374 bf16 TFLOP/s) and are not built.  Every wait is
 // bounded (device_sync.cuh); the epilogue warps wait with a sleep between
@@ -70,7 +78,7 @@ constexpr int THREADS = (2 + EPI_WARPS) * 32;
 constexpr int MAX_GROUPS = 64;
 constexpr int MAX_STAGES = 16;
 constexpr size_t SMEM_BYTES = 1024 + RING_BYTES + 1024;
-constexpr int kSmallChunks = 16;                      // BF16x3: small products drained every 16 chunks
+constexpr int kSmallK = 2048;                         // BF16x3: K between small-product drains
 constexpr uint32_t kSmallCol = 384;                   // BF16x3: TMEM column of the small-product accumulator
 
 struct TcGroup {
@@ -88,6 +96,7 @@ static_assert(sizeof(TcGroup) == 32, "group record layout");
 struct TcArgs {
     int M, N;
     int kblocks, chunk_kblocks, nchunks;
+    int small_every;  // BF16x3: chunks between small-product drains
     int ngroups;
     int tiles_m, tiles_n, tiles;
     int nstages;
@@ -156,11 +165,31 @@ struct Ring {
     }
 };
 
-// BF16x3 drains of the small-product accumulator: every kSmallChunks chunks and
-// at the last chunk of a tile (both the MMA issuer and the epilogue use this)
-__device__ __forceinline__ bool small_drain_after(int c, int nchunks)
+// 4 x 4 transpose inside each group of 4 lanes: lane 4g + r holds row r of its
+// group's block in v[0..3] on entry and column r on exit.  Each butterfly stage
+// m swaps the off-diagonal m x m sub-blocks: the lane without bit m trades its
+// elements with bit m set for its partner's elements without it.
+__device__ __forceinline__ void transpose4(double (&v)[4], int lane)
 {
-    return c == nchunks - 1 || (c % kSmallChunks) == kSmallChunks - 1;
+#pragma unroll
+    for (int m = 2; m >= 1; m >>= 1) {
+        const bool upper = (lane & m) != 0;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            if (e & m) continue;
+            const double send = upper ? v[e] : v[e | m];
+            const double got = __shfl_xor_sync(0xffffffffu, send, m);
+            if (upper) v[e] = got;
+            else v[e | m] = got;
+        }
+    }
+}
+
+// BF16x3 drains of the small-product accumulator: every `every` chunks (2048 of
+// K) and at the last chunk of a tile (both the MMA issuer and the epilogue use this)
+__device__ __forceinline__ bool small_drain_after(int c, int nchunks, int every)
+{
+    return c == nchunks - 1 || (c % every) == every - 1;
 }
 
 template <bool DF32>
@@ -328,7 +357,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_terms_kernel(const __grid_const
                         tc_commit(&acc_full[b.s]);
                         b.next(NBUF);
                         if constexpr (DF32) {
-                            if (small_drain_after(c, p.nchunks)) {
+                            if (small_drain_after(c, p.nchunks, p.small_every)) {
                                 tc_commit(small_full);
                                 ++small_drains;
                                 small_pending = true;
@@ -366,7 +395,11 @@ __global__ void __launch_bounds__(THREADS, 1) tc_terms_kernel(const __grid_const
             tile_coords(tile, p.tiles_m, p.tiles_n, tm, tn);
             for (int c = 0; c < p.nchunks && ok; ++c) {
                 for (int gi = 0; gi < p.ngroups; ++gi) {
-                    if (!mbar_wait_backoff(&acc_full[b.s], b.ph, p.err, kErrWaitMma)) { ok = false; break; }
+                    // every lane gives up together (the warp shuffles and syncs below need all 32)
+                    if (!__all_sync(0xffffffffu, mbar_wait_backoff(&acc_full[b.s], b.ph, p.err, kErrWaitMma))) {
+                        ok = false;
+                        break;
+                    }
                     tc_fence_after();
                     const uint32_t t0 = tmem_base + lane_off + (uint32_t)b.s * BUF_COLS + (uint32_t)(quarter * 32);
                     if constexpr (DF32) {
@@ -410,9 +443,10 @@ __global__ void __launch_bounds__(THREADS, 1) tc_terms_kernel(const __grid_const
                     if (lane == 0) mbar_arrive(&acc_empty[b.s]);
                     b.next(NBUF);
                     if constexpr (DF32) {
-                        if (small_drain_after(c, p.nchunks)) {
+                        if (small_drain_after(c, p.nchunks, p.small_every)) {
                             // the small products (2^-8 of hh and below) go straight into lo
-                            if (!mbar_wait_backoff(small_full, small_drains & 1u, p.err, kErrWaitMma)) {
+                            if (!__all_sync(0xffffffffu,
+                                            mbar_wait_backoff(small_full, small_drains & 1u, p.err, kErrWaitMma))) {
                                 ok = false;
                                 break;
                             }
@@ -436,32 +470,48 @@ __global__ void __launch_bounds__(THREADS, 1) tc_terms_kernel(const __grid_const
                 }
             }
             if (!ok) break;
-            // final epilogue of this tile
-            const int64_t row = (int64_t)tm * BM + row_in_tile;
-            const int64_t col0 = (int64_t)tn * BN + quarter * 32;
-            if (row < p.M) {
-                const int re = (!DF32 && p.row_exp) ? p.row_exp[row] : 0;
+            // final epilogue of this tile, 4 columns at a time: each lane forms its own row's
+            // values, transpose4 hands lane 4g + j column j of rows 4g .. 4g + 3, and each store
+            // then covers 8 rows x 4 consecutive columns of C (whole 32-byte sectors for FP64)
+            const int64_t row_me = (int64_t)tm * BM + row_in_tile;
+            const int re = (!DF32 && p.row_exp && row_me < p.M) ? p.row_exp[row_me] : 0;
+            const int64_t row0 = (int64_t)tm * BM + q4 * 32 + (lane & ~3);
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int64_t col = col0 + j;
-                    const bool keep = p.tri == 0 || (p.tri == 1 ? col - row <= p.tri_off : col - row >= p.tri_off);
-                    if (col < p.N && keep) {
-                        double v;
-                        if constexpr (DF32) {
-                            // no operand scaling in this form
-                            v = p.alpha * ((double)unpack2(hi2[j >> 1], j & 1) + (double)unpack2(lo2[j >> 1], j & 1));
-                        } else {
-                            const int ce = p.col_exp ? p.col_exp[col] : 0;
-                            v = p.alpha * ldexp(acc[j], re + ce);
-                        }
-                        if (p.c_fp32) {
-                            float* cp = static_cast<float*>(p.C) + row * p.ldc + col;
-                            if (p.read_c) v = fma(p.beta, (double)*cp, v);
-                            *cp = (float)v;
-                        } else {
-                            double* cp = static_cast<double*>(p.C) + row * p.ldc + col;
-                            if (p.read_c) v = fma(p.beta, *cp, v);
-                            *cp = v;
+            for (int pass = 0; pass < 8; ++pass) {
+                const int64_t c0 = (int64_t)tn * BN + quarter * 32 + pass * 4;
+                double v[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int jj = pass * 4 + j;
+                    if constexpr (DF32) {
+                        // no operand scaling in this form
+                        v[j] = p.alpha *
+                               ((double)unpack2(hi2[jj >> 1], jj & 1) + (double)unpack2(lo2[jj >> 1], jj & 1));
+                    } else {
+                        const int ce = (p.col_exp && c0 + j < p.N) ? p.col_exp[c0 + j] : 0;
+                        v[j] = p.alpha * ldexp(acc[jj], re + ce);
+                    }
+                }
+                transpose4(v, lane);
+                const int64_t col = c0 + (lane & 3);
+                if (col < p.N) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int64_t row = row0 + i;
+                        const bool keep =
+                            p.tri == 0 || (p.tri == 1 ? col - row <= p.tri_off : col - row >= p.tri_off);
+                        if (row < p.M && keep) {
+                            const int64_t off = row * p.ldc + col;
+                            double w = v[i];
+                            if (p.c_fp32) {
+                                float* cp = static_cast<float*>(p.C) + off;
+                                if (p.read_c) w = fma(p.beta, (double)*cp, w);
+                                *cp = (float)w;
+                            } else {
+                                double* cp = static_cast<double*>(p.C) + off;
+                                if (p.read_c) w = fma(p.beta, *cp, w);
+                                *cp = w;
+                            }
                         }
                     }
                 }
@@ -659,6 +709,7 @@ int launch_tc_terms(const TcProblem& P, void* stream, std::string& why)
     a.kblocks = (int)(P.k_pad / BK);
     a.chunk_kblocks = std::max(1, P.chunk / BK);
     a.nchunks = (a.kblocks + a.chunk_kblocks - 1) / a.chunk_kblocks;
+    a.small_every = std::max(1, kSmallK / (a.chunk_kblocks * BK));
     a.ngroups = P.ngroups;
     a.tiles_n = (int)((P.N + BN - 1) / BN);
     a.tiles_m = (int)((P.M + BM - 1) / BM);

@@ -22,16 +22,17 @@ scale: relative to each row's and column's largest entry, not to (|A||B|)_ij, be
 digits are cut from the row's fixed-point value.
 
 BF16x3 form (x = h + m + l, each the bf16 rounding of what is left; products hh, hm, mh, hl,
-mm, lh; the leading product hh in its own FP32 tensor-core accumulator drained every 128 of K
-into double-float registers, the five small products in a second accumulator drained every
-2048 of K):
+mm, lh; the leading product hh in its own FP32 tensor-core accumulator drained every L of K
+(L = 512) into double-float registers, the five small products in a second accumulator drained
+every 2048 of K):
     splitting and dropped products (ml, lm, ll):   <= 2^-25 |x| |y| per k
-    hh accumulation inside one 128-long chunk:      8 MMA additions, each rounding toward zero by
-                                                    at most one ulp of the running sum, plus the
-                                                    MMA's own 16-term sum: <= 2^-19 |x| |y|
+    hh accumulation inside one L-long chunk:        L / 16 MMA additions, each rounding toward
+                                                    zero by at most one ulp (2^-23) of the running
+                                                    sum, <= (L / 16) 2^-23 |x| |y|, plus the MMA's
+                                                    own 16-term sum, <= 2^-20 |x| |y|
     small products inside one 2048-long stretch:    640 additions to a sum below 2^-7 of
                                                     sum |x| |y|: <= 2^-20 |x| |y|
-    together (the accumulation term below):         <= 2^-18 |x| |y|
+    together (the accumulation term below):         ((L / 16) 2^-23 + 2^-19) |x| |y|
     the result rounded to FP32 (once per K chunk):  kc 2^-24 (|alpha| (|A||B|)_ij + |beta| |C0_ij|)
 """
 import math
@@ -72,15 +73,19 @@ def ozaki_bound(Aop, Bop, alpha, beta, C0, S, kchunks=1):
     return SLACK * (abs(alpha) * (trunc + dropped + acc) + out + oracle_rounding)
 
 
-def bf16x3_bound(Aop, Bop, alpha, beta, C0, kchunks=1):
-    """Elementwise bound for FP32 op(A) times op(B) in the BF16x3 form (result rounded to FP32)."""
+BF16X3_DRAIN = 512
+
+
+def bf16x3_bound(Aop, Bop, alpha, beta, C0, kchunks=1, drain=BF16X3_DRAIN):
+    """Elementwise bound for FP32 op(A) times op(B) in the BF16x3 form (result rounded to FP32),
+    the leading product's accumulator drained every `drain` of K."""
     Aop = np.asarray(Aop, dtype=np.float64)
     Bop = np.asarray(Bop, dtype=np.float64)
     K = Aop.shape[1]
     AB = np.abs(Aop) @ np.abs(Bop)
     cterm = 0.0 if C0 is None or beta == 0 else abs(beta) * np.abs(C0)
     split = 2.0 ** -25 * AB
-    accum = 2.0 ** -18 * AB
+    accum = ((drain / 16) * 2.0 ** -23 + 2.0 ** -19) * AB
     out = (kchunks + 1) * 2.0 ** -24 * (abs(alpha) * AB + cterm)
     oracle_rounding = (K + 2) * 2.0 ** -53 * (abs(alpha) * AB + cterm)
     return SLACK * (abs(alpha) * (split + accum) + out + oracle_rounding)

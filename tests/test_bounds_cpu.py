@@ -113,3 +113,69 @@ def test_bf16x3_split_inside_bound():
     assert worst_ratio(six, exact, 2.0 ** -25 * AB) <= 1.0
     bound = bf16x3_bound(A, B, 1.0, 0.0, None)
     assert worst_ratio(six - ha @ mb, exact, bound) > 1.0
+
+
+def _rz32(x):
+    """float64 values rounded toward zero to FP32 (the tensor cores' accumulator rounding)"""
+    x = np.asarray(x, dtype=np.float64)
+    r = x.astype(np.float32)
+    over = np.abs(r.astype(np.float64)) > np.abs(x)
+    r[over] = np.nextafter(r[over], np.float32(0))
+    return r
+
+
+def _pieces(x):
+    h = _bf16(x)
+    r1 = (x - h).astype(np.float32)
+    m = _bf16(r1)
+    r2 = (r1 - m).astype(np.float32)
+    return [p.astype(np.float64) for p in (h, m, _bf16(r2))]
+
+
+def bf16x3_emulate(A, B, drain, small_k=2048):
+    """The BF16x3 form's accumulation: every 16-long K step of a piece product is summed exactly
+    (one MMA) and added into an FP32 accumulator that rounds toward zero; hh has its own
+    accumulator, emptied into an exact sum every `drain` of K, and the five small products share
+    one emptied every `small_k` of K."""
+    ha, ma, la = _pieces(A)
+    hb, mb, lb = _pieces(B)
+    small = [(ha, mb), (ma, hb), (ha, lb), (ma, mb), (la, hb)]
+    K = A.shape[1]
+    total = np.zeros((A.shape[0], B.shape[1]))
+    acc_h = np.zeros_like(total, dtype=np.float32)
+    acc_s = np.zeros_like(total, dtype=np.float32)
+    for k0 in range(0, K, 16):
+        k1 = min(K, k0 + 16)
+        acc_h = _rz32(acc_h.astype(np.float64) + ha[:, k0:k1] @ hb[k0:k1])
+        acc_s = _rz32(acc_s.astype(np.float64) + sum(a[:, k0:k1] @ b[k0:k1] for a, b in small))
+        if k1 % drain == 0 or k1 == K:
+            total += acc_h
+            acc_h[:] = 0
+        if k1 % small_k == 0 or k1 == K:
+            total += acc_s
+            acc_s[:] = 0
+    return total
+
+
+@pytest.mark.parametrize("drain", [128, 512])
+def test_bf16x3_accumulation_inside_bound(drain):
+    """Round-toward-zero accumulation with drains every `drain` of K sits inside the bound for
+    that drain length without its slack; positive inputs make every rounding error point the
+    same way (the worst case for a truncating accumulator)."""
+    rng = np.random.default_rng(11)
+    A = rng.uniform(0, 1, (6, 4096)).astype(np.float32)
+    B = rng.uniform(0, 1, (4096, 5)).astype(np.float32)
+    exact = A.astype(np.float64) @ B.astype(np.float64)
+    got = bf16x3_emulate(A, B, drain)
+    assert worst_ratio(got, exact, bf16x3_bound(A, B, 1.0, 0.0, None, drain=drain) / SLACK) <= 1.0
+
+
+def test_bf16x3_bound_catches_an_undrained_accumulator():
+    """Without the periodic drains (one accumulator over the whole K = 16384, 1024 truncating
+    additions) the error leaves the bound for drains every 512 of K."""
+    rng = np.random.default_rng(12)
+    A = rng.uniform(0, 1, (6, 16384)).astype(np.float32)
+    B = rng.uniform(0, 1, (16384, 5)).astype(np.float32)
+    exact = A.astype(np.float64) @ B.astype(np.float64)
+    got = bf16x3_emulate(A, B, drain=16384, small_k=16384)
+    assert worst_ratio(got, exact, bf16x3_bound(A, B, 1.0, 0.0, None, drain=512)) > 1.0
