@@ -618,6 +618,8 @@ def run_batched_bench(args, w, world, rank, local, pg):
     if rank != 0:
         return
     s0 = stats[0][0]
+    if s0.mb == 0:  # grouped path: problems multiplied whole, nothing planned
+        planner = "none: every problem fits whole in half the budget, grouped (%d groups)" % s0.steps
     pk, pk_src = peaks()
     # the two halves' kernels overlap, so the summed kernel time over-counts: device time instead
     achieved = flops * n_steps / dev_s / 1e12 if dev_s > 0 else None

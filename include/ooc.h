@@ -153,8 +153,10 @@ typedef struct {
  * the same transposes are packed into one half (at most 64 per group), copied
  * in with one copy per operand, multiplied by one persistent launch over all
  * their tiles and copied out, groups alternating halves so that one group's
- * copies overlap the other's kernel; stats->steps then counts groups and
- * stats->blocks problems.  Otherwise consecutive problems alternate halves
+ * copies overlap the other's kernel; stats->steps then counts groups,
+ * stats->blocks problems, and stats->mb / nb / kb stay 0: grouped problems are
+ * not planned, so opts' planner flags (OOC_PLAN_MODEL) have no effect there.
+ * Otherwise consecutive problems alternate halves
  * and compute streams, so the copies and kernels of problem g + 1 overlap
  * problem g, while problem g + 2 waits for problem g to finish; each problem
  * is planned for half the budget with opts (form: FP64 or Ozaki).
