@@ -127,15 +127,20 @@ __device__ __forceinline__ void tile_coords(int tile, int tiles_m, int tiles_n, 
     tn = r / rows;
 }
 
-// Exact FP32 integer x (|x| < 2^24) times 2^e as a double, built from the bit
-// fields with integer operations (no conversion or multiply on the FP64 pipe).
-__device__ __forceinline__ double scaled_f32_to_f64(uint32_t xb, int e)
+// Exact FP32 integer x (1 <= |x| < 2^24, or 0) times 2^e as a double, built
+// from the bit fields with 32-bit integer operations (no conversion or multiply
+// on the FP64 pipe, few instructions on the warps that share the MMA thread's
+// sub-partition): `bias_hi` = (1023 - 127 + e) << 20 moves the FP32 exponent
+// field, shifted into the double's high word, to the double's bias and scale;
+// the low 3 mantissa bits go to the top of the low word.  The exponent field
+// e8 + 896 + e (127 <= e8 <= 150) stays inside 1..2046 and the bias inside its
+// 11 bits for -896 <= e <= 1000; the digit weights -6 (s + t) are at least -66.
+__device__ __forceinline__ double scaled_f32_to_f64(uint32_t xb, uint32_t bias_hi)
 {
-    if ((xb & 0x7FFFFFFFu) == 0u) return 0.0;
-    const uint64_t sign = (uint64_t)(xb >> 31) << 63;
-    const uint64_t ex = (uint64_t)((int)((xb >> 23) & 0xFFu) - 127 + 1023 + e) << 52;
-    const uint64_t man = (uint64_t)(xb & 0x7FFFFFu) << 29;
-    return __longlong_as_double((long long)(sign | ex | man));
+    const uint32_t mag = xb & 0x7FFFFFFFu;
+    const uint32_t hi = ((mag >> 3) + bias_hi) | (xb & 0x80000000u);
+    const uint32_t lo = xb << 29;
+    return mag ? __hiloint2double((int)hi, (int)lo) : 0.0;
 }
 
 // Packed pairs of FP32 values (element 2j in the low half): Blackwell's f32x2
@@ -421,7 +426,8 @@ __global__ void __launch_bounds__(THREADS, 1) tc_terms_kernel(const __grid_const
                             }
                         }
                     } else {
-                        const int e0 = p.g[gi].scale_exp, e1 = p.g[gi].scale_exp2;
+                        const uint32_t e0 = (uint32_t)(896 + p.g[gi].scale_exp) << 20;
+                        const uint32_t e1 = (uint32_t)(896 + p.g[gi].scale_exp2) << 20;
                         const bool has_second = p.g[gi].np > 1;
 #pragma unroll
                         for (int cc = 0; cc < 2; ++cc) {
@@ -734,6 +740,10 @@ int launch_tc_terms(const TcProblem& P, void* stream, std::string& why)
         d.scale_exp2 = (int16_t)s.scale_exp2;
         if (!P.df32 && s.np > 2) {
             why = "exact (Ozaki) groups hold at most two pairs";
+            return OOC_ERR_INVALID_ARG;
+        }
+        if (!P.df32 && (s.scale_exp < -896 || s.scale_exp > 1000 || s.scale_exp2 < -896 || s.scale_exp2 > 1000)) {
+            why = "digit weight outside the drain's exponent range";
             return OOC_ERR_INVALID_ARG;
         }
         max_stage = std::max(max_stage, (uint32_t)s.na * A_TILE + (uint32_t)s.nb * B_TILE);
