@@ -479,6 +479,10 @@ __global__ void __launch_bounds__(THREADS, 1) tc_terms_kernel(const __grid_const
             // final epilogue of this tile, 4 columns at a time: each lane forms its own row's
             // values, transpose4 hands lane 4g + j column j of rows 4g .. 4g + 3, and each store
             // then covers 8 rows x 4 consecutive columns of C (whole 32-byte sectors for FP64)
+            // BF16x3 forms alpha * (hi + lo) + beta * C_old in FP32 double-float steps (TwoSum,
+            // products split with fma) and rounds once at the end: on this part the FP64 pipe
+            // would take ~18 us per tile for it, holding the accumulators the MMAs wait for
+            const float alpha_f = (float)p.alpha, beta_f = (float)p.beta;
             const int64_t row_me = (int64_t)tm * BM + row_in_tile;
             const int re = (!DF32 && p.row_exp && row_me < p.M) ? p.row_exp[row_me] : 0;
             const int64_t row0 = (int64_t)tm * BM + q4 * 32 + (lane & ~3);
@@ -490,9 +494,13 @@ __global__ void __launch_bounds__(THREADS, 1) tc_terms_kernel(const __grid_const
                 for (int j = 0; j < 4; ++j) {
                     const int jj = pass * 4 + j;
                     if constexpr (DF32) {
-                        // no operand scaling in this form
-                        v[j] = p.alpha *
-                               ((double)unpack2(hi2[jj >> 1], jj & 1) + (double)unpack2(lo2[jj >> 1], jj & 1));
+                        // no operand scaling in this form; (ph, pl) = alpha * (hi + lo), packed
+                        const float hi = unpack2(hi2[jj >> 1], jj & 1), lo = unpack2(lo2[jj >> 1], jj & 1);
+                        const float sh = __fadd_rn(hi, lo), bp = __fsub_rn(sh, hi);
+                        const float sl = __fadd_rn(__fsub_rn(hi, __fsub_rn(sh, bp)), __fsub_rn(lo, bp));
+                        const float ph = __fmul_rn(alpha_f, sh);
+                        const float pl = __fmaf_rn(alpha_f, sl, __fmaf_rn(alpha_f, sh, -ph));
+                        v[j] = __longlong_as_double((long long)pack2(__float_as_uint(ph), __float_as_uint(pl)));
                     } else {
                         const int ce = (p.col_exp && c0 + j < p.N) ? p.col_exp[c0 + j] : 0;
                         v[j] = p.alpha * ldexp(acc[jj], re + ce);
@@ -508,6 +516,24 @@ __global__ void __launch_bounds__(THREADS, 1) tc_terms_kernel(const __grid_const
                             p.tri == 0 || (p.tri == 1 ? col - row <= p.tri_off : col - row >= p.tri_off);
                         if (row < p.M && keep) {
                             const int64_t off = row * p.ldc + col;
+                            if constexpr (DF32) {
+                                const uint64_t b = (uint64_t)__double_as_longlong(v[i]);
+                                const float ph = unpack2(b, 0), pl = unpack2(b, 1);
+                                float* cp = static_cast<float*>(p.C) + off;
+                                float w;
+                                if (p.read_c) {
+                                    // beta * c = qh + ql and ph + qh = th + tl exactly; one rounding left
+                                    const float c = *cp;
+                                    const float qh = __fmul_rn(beta_f, c), ql = __fmaf_rn(beta_f, c, -qh);
+                                    const float th = __fadd_rn(ph, qh), bq = __fsub_rn(th, ph);
+                                    const float tl = __fadd_rn(__fsub_rn(ph, __fsub_rn(th, bq)), __fsub_rn(qh, bq));
+                                    w = __fadd_rn(th, __fadd_rn(tl, __fadd_rn(pl, ql)));
+                                } else {
+                                    w = __fadd_rn(ph, pl);
+                                }
+                                *cp = w;
+                                continue;
+                            }
                             double w = v[i];
                             if (p.c_fp32) {
                                 float* cp = static_cast<float*>(p.C) + off;
@@ -740,6 +766,10 @@ int launch_tc_terms(const TcProblem& P, void* stream, std::string& why)
         d.scale_exp2 = (int16_t)s.scale_exp2;
         if (!P.df32 && s.np > 2) {
             why = "exact (Ozaki) groups hold at most two pairs";
+            return OOC_ERR_INVALID_ARG;
+        }
+        if (P.df32 && (!P.c_fp32 || (double)(float)P.alpha != P.alpha || (double)(float)P.beta != P.beta)) {
+            why = "the BF16x3 form writes FP32 C with FP32 alpha and beta";
             return OOC_ERR_INVALID_ARG;
         }
         if (!P.df32 && (s.scale_exp < -896 || s.scale_exp > 1000 || s.scale_exp2 < -896 || s.scale_exp2 > 1000)) {
