@@ -103,6 +103,8 @@ typedef struct {
     int32_t slices;          /* Ozaki slices / BF16x3 pieces used                    */
     int32_t products;        /* slice products per tile                              */
     int64_t kernel_launches; /* kernels the call launched (tile + split kernels)    */
+    double split_seconds;    /* share of kernel_seconds spent in the split forms'
+                                splitting kernels (0 for FP64 and in graph mode)    */
 } ooc_stats;
 
 /*

@@ -45,7 +45,7 @@ class ooc_stats(ctypes.Structure):
                 ("depth", ctypes.c_int32), ("c_buffers", ctypes.c_int32), ("b_buffers", ctypes.c_int32),
                 ("form", ctypes.c_int32), ("blocks", ctypes.c_int64), ("steps", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64), ("slices", ctypes.c_int32), ("products", ctypes.c_int32),
-                ("kernel_launches", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("split_seconds", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -623,7 +623,7 @@ struct Driver {
     char* arena = nullptr;
     size_t bytes = 0;
     Dev d;
-    double h2d = 0, d2h = 0, kernel_s = 0;
+    double h2d = 0, d2h = 0, kernel_s = 0, split_s = 0;
     int64_t steps = 0, launches = 0;
     ooc_opts gemm_opts;
     std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
@@ -686,6 +686,7 @@ struct Driver {
         h2d += st.h2d_bytes;
         d2h += st.d2h_bytes;
         kernel_s += st.kernel_seconds;
+        split_s += st.split_seconds;
         launches += st.kernel_launches;
         ++steps;
         return OOC_OK;
@@ -730,6 +731,7 @@ struct Driver {
         stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         stats->device_seconds = stats->seconds;
         stats->kernel_seconds = kernel_s;
+        stats->split_seconds = split_s;
         stats->tflops = stats->seconds > 0 ? flops / stats->seconds / 1e12 : 0.0;
         stats->h2d_bytes = h2d;
         stats->d2h_bytes = d2h;

@@ -372,6 +372,8 @@ struct Exec {
     long n_copy = 0, n_kern = 0;
     std::vector<cudaEvent_t> ev;
     std::vector<cudaEvent_t> kev;  // timing pairs around tile kernels
+    std::vector<cudaEvent_t> kmid;  // split forms: between a tile's split kernels and its contraction
+    std::vector<char> kmid_set;
     std::vector<TraceRec> trace;
     std::vector<int64_t> gen, split_gen;  // loads into each slot / loads already split (split forms)
     int64_t launches = 0;                 // kernels launched by this call
@@ -388,6 +390,7 @@ struct Exec {
             if (s) cudaStreamSynchronize(s);
         for (auto& e : ev) { if (e) cudaEventDestroy(e); e = nullptr; }
         for (auto& e : kev) { if (e) cudaEventDestroy(e); e = nullptr; }
+        for (auto& e : kmid) { if (e) cudaEventDestroy(e); e = nullptr; }
         for (auto& r : trace) { if (r.e0) cudaEventDestroy(r.e0); if (r.e1) cudaEventDestroy(r.e1); }
         trace.clear();
         if (t_begin) cudaEventDestroy(t_begin);
@@ -458,6 +461,13 @@ int launch_split_tile(const Plan& p, const Op& op, Exec& x, const Operands& o, i
         }
         if (rc) return rc;
         x.split_gen[s] = x.gen[s];
+    }
+    if (x.time_kernels && x.n_kern < (long)x.kmid.size()) {
+        if (cudaEventRecord(x.kmid[x.n_kern], static_cast<cudaStream_t>(st)) != cudaSuccess) {
+            why = "split timing event";
+            return OOC_ERR_CUDA;
+        }
+        x.kmid_set[x.n_kern] = 1;
     }
     TcProblem P;
     P.M = rows; P.N = cols; P.k_pad = K > 0 ? k_pad : 0;
@@ -629,6 +639,9 @@ int execute(Exec& x, const std::vector<Op>& ops, const Operands& o, int es, cons
     for (const Op& op : ops) nkern += op.kind == kKernel;
     x.kev.resize(2 * nkern, nullptr);
     for (auto& e : x.kev) CK(cudaEventCreate(&e));
+    x.kmid.resize(nkern, nullptr);
+    for (auto& e : x.kmid) CK(cudaEventCreate(&e));
+    x.kmid_set.assign(nkern, 0);
     CK(cudaEventCreate(&x.t_begin));
     for (auto& e : x.t_end) CK(cudaEventCreate(&e));
 
@@ -674,13 +687,18 @@ int execute(Exec& x, const std::vector<Op>& ops, const Operands& o, int es, cons
             CK(cudaEventElapsedTime(&ms, x.t_begin, e));
             best = std::max(best, ms);
         }
-        double ksum = 0;
+        double ksum = 0, ssum = 0;
         for (int64_t k = 0; k < x.n_kern; ++k) {
             CK(cudaEventElapsedTime(&ms, x.kev[2 * k], x.kev[2 * k + 1]));
             ksum += ms;
+            if (x.kmid_set[k]) {
+                CK(cudaEventElapsedTime(&ms, x.kev[2 * k], x.kmid[k]));
+                ssum += ms;
+            }
         }
         stats->device_seconds = best * 1e-3;
         stats->kernel_seconds = ksum * 1e-3;
+        stats->split_seconds = ssum * 1e-3;
         stats->h2d_bytes = x.h2d;
         stats->d2h_bytes = x.d2h;
         stats->mb = p.mb; stats->nb = p.nb; stats->kb = p.kb;
@@ -1138,6 +1156,9 @@ int run_batched(int32_t count, const ooc_gemm_desc* d, size_t budget, const ooc_
     for (auto& e : x.ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     x.kev.resize(2 * nkern, nullptr);
     for (auto& e : x.kev) CK(cudaEventCreate(&e));
+    x.kmid.resize(nkern, nullptr);
+    for (auto& e : x.kmid) CK(cudaEventCreate(&e));
+    x.kmid_set.assign(nkern, 0);
     CK(cudaEventCreate(&x.t_begin));
     for (auto& e : x.t_end) CK(cudaEventCreate(&e));
     const int ev_done0 = 2 * E, ev_fork = 2 * E + 2;
@@ -1221,13 +1242,18 @@ int run_batched(int32_t count, const ooc_gemm_desc* d, size_t budget, const ooc_
             CK(cudaEventElapsedTime(&ms, x.t_begin, e));
             best = std::max(best, ms);
         }
-        double ksum = 0;
+        double ksum = 0, ssum = 0;
         for (int64_t k = 0; x.time_kernels && k < x.n_kern; ++k) {
             CK(cudaEventElapsedTime(&ms, x.kev[2 * k], x.kev[2 * k + 1]));
             ksum += ms;
+            if (x.kmid_set[k]) {
+                CK(cudaEventElapsedTime(&ms, x.kev[2 * k], x.kmid[k]));
+                ssum += ms;
+            }
         }
         stats->device_seconds = best * 1e-3;
         stats->kernel_seconds = ksum * 1e-3;  // 0 in graph mode (not timed)
+        stats->split_seconds = ssum * 1e-3;
         stats->h2d_bytes = x.h2d;
         stats->d2h_bytes = x.d2h;
         for (int g = 0; g < count; ++g) {
@@ -1629,7 +1655,7 @@ struct ooc_session {
     cudaStream_t st[3] = {nullptr, nullptr, nullptr};
     size_t c_slot = 0, header = 256;
     int64_t ldc_dev = 0;
-    double h2d = 0, d2h = 0, kernel_s = 0, device_s = 0, flops = 0;
+    double h2d = 0, d2h = 0, kernel_s = 0, split_s = 0, device_s = 0, flops = 0;
     int64_t launches = 0, steps = 0;
     std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
 
@@ -1778,6 +1804,7 @@ int ooc_session_step(ooc_session* s, char transA, char transB, int64_t K, double
     s->h2d += st.h2d_bytes;
     s->d2h += st.d2h_bytes;
     s->kernel_s += st.kernel_seconds;
+    s->split_s += st.split_seconds;
     s->device_s += st.device_seconds;
     s->launches += st.kernel_launches;
     s->steps += st.steps;
@@ -1838,6 +1865,7 @@ int ooc_session_finish(ooc_session* s, ooc_stats* stats)
         stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - s->t0).count();
         stats->device_seconds = s->device_s;
         stats->kernel_seconds = s->kernel_s;
+        stats->split_seconds = s->split_s;
         stats->tflops = stats->seconds > 0 ? s->flops / stats->seconds / 1e12 : 0.0;
         stats->h2d_bytes = s->h2d;
         stats->d2h_bytes = s->d2h;

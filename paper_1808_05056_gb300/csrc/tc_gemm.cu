@@ -604,6 +604,54 @@ __global__ void __launch_bounds__(256) split_bf16x3_kernel(const float* __restri
     }
 }
 
+// The same split for a K-major source whose rows start on 16-byte boundaries
+// (the A slots of row-major operands): thread (k8, row) splits 8 consecutive K
+// with two 16-byte loads and one 16-byte store per piece plane; no staging.
+// Grid: x over k_pad / 8 in blocks of 256 threads, y over rows_pad.
+__device__ __forceinline__ uint32_t bf16_pair(float a, float b)
+{
+    return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(a)) |
+           ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(b)) << 16);
+}
+
+__global__ void __launch_bounds__(256) split_bf16x3_rows_kernel(const float* __restrict__ X, int64_t sr, int rows,
+                                                                int K, int rows_pad, int k_pad,
+                                                                __nv_bfloat16* __restrict__ planes)
+{
+    const int r = blockIdx.y;
+    const int k = (blockIdx.x * blockDim.x + threadIdx.x) * 8;
+    if (k >= k_pad) return;
+    float x[8];
+    if (r < rows && k + 8 <= K) {
+        const float4* src = reinterpret_cast<const float4*>(X + (int64_t)r * sr + k);
+        const float4 a = __ldg(src), b = __ldg(src + 1);
+        x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+        x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+    } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) x[j] = (r < rows && k + j < K) ? X[(int64_t)r * sr + k + j] : 0.f;
+    }
+    uint32_t hw[4], mw[4], lw[4];
+#pragma unroll
+    for (int j = 0; j < 8; j += 2) {
+        float h2[2], r1[2], m2[2], r2[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            h2[q] = __bfloat162float(__float2bfloat16_rn(x[j + q]));
+            r1[q] = x[j + q] - h2[q];
+            m2[q] = __bfloat162float(__float2bfloat16_rn(r1[q]));
+            r2[q] = r1[q] - m2[q];
+        }
+        hw[j / 2] = bf16_pair(h2[0], h2[1]);
+        mw[j / 2] = bf16_pair(m2[0], m2[1]);
+        lw[j / 2] = bf16_pair(r2[0], r2[1]);
+    }
+    const size_t plane = (size_t)rows_pad * k_pad, o = (size_t)r * k_pad + k;
+    *reinterpret_cast<uint4*>(planes + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+    *reinterpret_cast<uint4*>(planes + plane + o) = make_uint4(mw[0], mw[1], mw[2], mw[3]);
+    *reinterpret_cast<uint4*>(planes + 2 * plane + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+}
+
 // max |x| over each row (as the bit pattern of a non-negative double, which
 // orders like its value); rowmax must start at zero
 __global__ void __launch_bounds__(256) rowmax_f64_kernel(const double* __restrict__ X, int64_t sr, int64_t sk,
@@ -696,9 +744,16 @@ int tc_max_groups() { return MAX_GROUPS; }
 int launch_split_bf16x3(const float* X, int64_t sr, int64_t sk, int rows, int K, int rows_pad, int k_pad, void* planes,
                         void* stream, std::string& why)
 {
-    dim3 grid((unsigned)((k_pad + ST - 1) / ST), (unsigned)((rows_pad + ST - 1) / ST));
-    split_bf16x3_kernel<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(
-        X, sr, sk, rows, K, rows_pad, k_pad, static_cast<__nv_bfloat16*>(planes));
+    if (sk == 1 && sr % 4 == 0 && reinterpret_cast<uintptr_t>(X) % 16 == 0 && k_pad % 8 == 0 &&
+        reinterpret_cast<uintptr_t>(planes) % 16 == 0 && rows_pad <= 65535) {
+        dim3 grid((unsigned)((k_pad / 8 + 255) / 256), (unsigned)rows_pad);
+        split_bf16x3_rows_kernel<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+            X, sr, rows, K, rows_pad, k_pad, static_cast<__nv_bfloat16*>(planes));
+    } else {
+        dim3 grid((unsigned)((k_pad + ST - 1) / ST), (unsigned)((rows_pad + ST - 1) / ST));
+        split_bf16x3_kernel<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+            X, sr, sk, rows, K, rows_pad, k_pad, static_cast<__nv_bfloat16*>(planes));
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) { why = std::string("split_bf16x3: ") + cudaGetErrorString(e); return OOC_ERR_CUDA; }
     return OOC_OK;

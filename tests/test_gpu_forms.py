@@ -185,3 +185,16 @@ def test_ozaki_bad_digit_count(ooc):
         rc = ooc.ooc_dgemm("N", "N", 8, 8, 8, 1.0, A, 8, A, 8, 0.0, C, 8, 1 << 20,
                            ooc.make_opts(form=ooc.OOC_FORM_OZAKI, slices=S), None)
         assert rc == ooc.OOC_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("form", ["bf16x3", "ozaki", "fp64"])
+def test_split_kernel_time_reported(ooc, form):
+    """stats.split_seconds is the split kernels' share of kernel_seconds: positive and below
+    it for the split forms, zero for FP64 (no split kernels)."""
+    f = {"bf16x3": ooc.OOC_FORM_BF16X3, "ozaki": ooc.OOC_FORM_OZAKI, "fp64": ooc.OOC_FORM_FP64}[form]
+    _, _, st = _run(ooc, f, "N", "N", 700, 600, 900, 1.0, 0.0, synth.UNIFORM, budget=8 << 20)
+    assert st.kernel_seconds > 0
+    if form == "fp64":
+        assert st.split_seconds == 0.0
+    else:
+        assert 0.0 < st.split_seconds < st.kernel_seconds
