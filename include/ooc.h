@@ -351,11 +351,16 @@ int ooc_plan(int64_t M, int64_t N, int64_t K, int32_t elem_bytes, int32_t beta_n
 /*
  * One operation of an issued pipeline schedule (host issue order), for
  * checking the Section IV buffer-hazard rule without a GPU.
- * kind: 0 H2D copy, 1 tile kernel, 2 D2H copy, 3 event record, 4 event wait.
+ * kind: 0 H2D copy, 1 tile kernel, 2 D2H copy, 3 event record, 4 event wait,
+ * 5 split (the split forms: the raw chunk in read_slot[0] into the bf16
+ * planes of write_slot).
  * stream: 0 H2D stream, 1 compute stream, 2 D2H stream.
  * A tag names the datum in a device slot: {matrix (0 A, 1 B, 2 C),
  * row chunk, column chunk, version}; a C block's version counts the K-chunks
- * folded into it.  Unused slots are -1.
+ * folded into it.  Unused slots are -1.  Plans of the split forms load A and B
+ * into raw staging areas, used in turn, and split them from there into the
+ * slots' planes: after the plan's S slots, ids S and S + 1 are A's areas and
+ * S + 2 (and S + 3 when B is loaded in K chunks) B's.
  */
 typedef struct {
     int32_t kind, stream, event, nreads;

@@ -374,6 +374,8 @@ struct Exec {
     std::vector<cudaEvent_t> kev;  // timing pairs around tile kernels
     std::vector<cudaEvent_t> kmid;  // split forms: between a tile's split kernels and its contraction
     std::vector<char> kmid_set;
+    std::vector<cudaEvent_t> sev;   // staged plans: timing pairs around split ops
+    long n_split = 0;
     std::vector<TraceRec> trace;
     std::vector<int64_t> gen, split_gen;  // loads into each slot / loads already split (split forms)
     int64_t launches = 0;                 // kernels launched by this call
@@ -391,6 +393,7 @@ struct Exec {
         for (auto& e : ev) { if (e) cudaEventDestroy(e); e = nullptr; }
         for (auto& e : kev) { if (e) cudaEventDestroy(e); e = nullptr; }
         for (auto& e : kmid) { if (e) cudaEventDestroy(e); e = nullptr; }
+        for (auto& e : sev) { if (e) cudaEventDestroy(e); e = nullptr; }
         for (auto& r : trace) { if (r.e0) cudaEventDestroy(r.e0); if (r.e1) cudaEventDestroy(r.e1); }
         trace.clear();
         if (t_begin) cudaEventDestroy(t_begin);
@@ -418,6 +421,34 @@ struct Exec {
 
 // Tensor-core forms: split each newly loaded A / B slot into bf16 planes (once
 // per load), then run the split-product tile kernel on the C block.
+// Split the raw data at src_slot (a slot, or a staged plan's staging area) of
+// operand A or B into the bf16 planes (and Ozaki row exponents) of dst_slot,
+// on the compute stream.
+int split_slot(const Plan& p, Exec& x, int src_slot, int dst_slot, bool is_a, int64_t nrows, int64_t K,
+               std::string& why)
+{
+    const bool ozaki = p.form == OOC_FORM_OZAKI;
+    const int S = split_planes(p);
+    const int64_t k_pad = split_k_pad(p);
+    const int64_t rpad = split_rows_pad(is_a ? p.mb : p.nb);
+    void* st = x.smap[kStreamCompute];
+    char* planes = x.base + slot_aux_offset(p, dst_slot);
+    int* exps = reinterpret_cast<int*>(planes + split_planes_bytes(p, is_a ? p.mb : p.nb));
+    // element (r, k) of the slot: K-major rows or K down the stored rows
+    const bool kmajor = is_a ? !p.ta : p.tb;
+    const int64_t ld = is_a ? p.lda_dev : p.ldb_dev;
+    const int64_t sr = kmajor ? ld : 1, sk = kmajor ? 1 : ld;
+    const char* src = x.base + slot_offset(p, src_slot);
+    x.launches += ozaki ? (K > 0 ? 3 : 2) : 1;
+    if (ozaki) {
+        auto* rowmax = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(exps) + ((rpad * 4 + 255) / 256) * 256);
+        return launch_split_ozaki(reinterpret_cast<const double*>(src), sr, sk, (int)nrows, (int)K, (int)rpad,
+                                  (int)k_pad, S, kOzakiBeta, planes, exps, rowmax, st, why);
+    }
+    return launch_split_bf16x3(reinterpret_cast<const float*>(src), sr, sk, (int)nrows, (int)K, (int)rpad, (int)k_pad,
+                               planes, st, why);
+}
+
 int launch_split_tile(const Plan& p, const Op& op, Exec& x, const Operands& o, int sa, int sb, int sc,
                       std::string& why)
 {
@@ -438,27 +469,11 @@ int launch_split_tile(const Plan& p, const Op& op, Exec& x, const Operands& o, i
         const int s = sides[q].slot;
         if (s < 0) continue;
         char* aux = x.base + slot_aux_offset(p, s);
-        const int64_t rpad = sides[q].is_a ? ra_pad : rb_pad;
         planes[q] = aux;
         exps[q] = reinterpret_cast<int*>(aux + split_planes_bytes(p, sides[q].is_a ? p.mb : p.nb));
-        if (x.split_gen[s] == x.gen[s]) continue;
-        const int nrows = (int)(sides[q].is_a ? rows : cols);
-        // element (r, k) of the slot: K-major rows or K down the stored rows
-        const bool kmajor = sides[q].is_a ? !p.ta : p.tb;
-        const int64_t ld = sides[q].is_a ? p.lda_dev : p.ldb_dev;
-        const int64_t sr = kmajor ? ld : 1, sk = kmajor ? 1 : ld;
-        const char* src = x.base + slot_offset(p, s);
-        int rc;
-        x.launches += ozaki ? (K > 0 ? 3 : 2) : 1;
-        if (ozaki) {
-            auto* rowmax = reinterpret_cast<unsigned long long*>(
-                reinterpret_cast<char*>(exps[q]) + ((rpad * 4 + 255) / 256) * 256);
-            rc = launch_split_ozaki(reinterpret_cast<const double*>(src), sr, sk, nrows, (int)K, (int)rpad,
-                                    (int)k_pad, S, kOzakiBeta, planes[q], exps[q], rowmax, st, why);
-        } else {
-            rc = launch_split_bf16x3(reinterpret_cast<const float*>(src), sr, sk, nrows, (int)K, (int)rpad, (int)k_pad,
-                                     planes[q], st, why);
-        }
+        // staged plans split in their own schedule ops; otherwise the first tile after a load splits it
+        if (p.staged || x.split_gen[s] == x.gen[s]) continue;
+        const int rc = split_slot(p, x, s, s, sides[q].is_a, sides[q].is_a ? rows : cols, K, why);
         if (rc) return rc;
         x.split_gen[s] = x.gen[s];
     }
@@ -543,9 +558,10 @@ int issue_ops(Exec& x, const Plan& p, const std::vector<Op>& ops, const Operands
     const auto t_issue0 = std::chrono::steady_clock::now();
     for (const Op& op : ops) {
         cudaStream_t s = x.smap[op.stream];
-        const bool traced = trace_path && (op.kind == kH2D || op.kind == kKernel || op.kind == kD2H);
+        const bool traced = trace_path && (op.kind == kH2D || op.kind == kKernel || op.kind == kD2H || op.kind == kSplit);
         if (traced) {
-            TraceRec r{op.kind, op.stream, op.i, op.j, op.kc, 0.0,
+            // a split is device work on the kernel stream: traced as a kernel
+            TraceRec r{op.kind == kSplit ? (int)kKernel : op.kind, op.stream, op.i, op.j, op.kc, 0.0,
                        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_issue0).count(),
                        nullptr, nullptr};
             CK(cudaEventCreate(&r.e0));
@@ -593,6 +609,20 @@ int issue_ops(Exec& x, const Plan& p, const std::vector<Op>& ops, const Operands
             }
             break;
         }
+        case kSplit: {
+            // staged plans: the staging area's raw chunk into the planes of the slot it is for
+            const Tag& t = op.wtag;
+            const bool is_a = t.m == kMatA;
+            const int64_t nrows = is_a ? p.rows_of(t.r) : p.cols_of(t.c);
+            const int64_t K = p.K > 0 ? p.k_of(is_a ? t.c : t.r) : 0;
+            const bool timed = x.time_kernels && 2 * x.n_split + 1 < (long)x.sev.size();
+            if (timed) CK(cudaEventRecord(x.sev[2 * x.n_split], s));
+            rc = split_slot(p, x, op.rslot[0], op.wslot, is_a, nrows, K, why);
+            if (rc) return fail(rc, why);
+            if (timed) CK(cudaEventRecord(x.sev[2 * x.n_split + 1], s));
+            ++x.n_split;
+            break;
+        }
         case kKernel: {
             if (inj.kernel >= 0 && x.n_kern == inj.kernel) return fail(OOC_ERR_INJECTED, "injected kernel failure");
             if (x.time_kernels) CK(cudaEventRecord(x.kev[2 * x.n_kern], s));
@@ -631,17 +661,22 @@ int execute(Exec& x, const std::vector<Op>& ops, const Operands& o, int es, cons
     const Plan& p = x.p;
     std::string why;
     int rc = OOC_OK;
-    x.gen.assign(p.slots(), 0);
-    x.split_gen.assign(p.slots(), -1);
+    x.gen.assign(p.slots() + 4, 0);  // + the staging areas of staged plans
+    x.split_gen.assign(p.slots() + 4, -1);
     x.ev.resize(n_events(p), nullptr);
     for (auto& e : x.ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-    int64_t nkern = 0;
-    for (const Op& op : ops) nkern += op.kind == kKernel;
+    int64_t nkern = 0, nsplit = 0;
+    for (const Op& op : ops) {
+        nkern += op.kind == kKernel;
+        nsplit += op.kind == kSplit;
+    }
     x.kev.resize(2 * nkern, nullptr);
     for (auto& e : x.kev) CK(cudaEventCreate(&e));
     x.kmid.resize(nkern, nullptr);
     for (auto& e : x.kmid) CK(cudaEventCreate(&e));
     x.kmid_set.assign(nkern, 0);
+    x.sev.resize(2 * nsplit, nullptr);
+    for (auto& e : x.sev) CK(cudaEventCreate(&e));
     CK(cudaEventCreate(&x.t_begin));
     for (auto& e : x.t_end) CK(cudaEventCreate(&e));
 
@@ -695,6 +730,11 @@ int execute(Exec& x, const std::vector<Op>& ops, const Operands& o, int es, cons
                 CK(cudaEventElapsedTime(&ms, x.kev[2 * k], x.kmid[k]));
                 ssum += ms;
             }
+        }
+        for (long k = 0; 2 * k + 1 < (long)x.sev.size() && k < x.n_split; ++k) {
+            CK(cudaEventElapsedTime(&ms, x.sev[2 * k], x.sev[2 * k + 1]));
+            ksum += ms;
+            ssum += ms;
         }
         stats->device_seconds = best * 1e-3;
         stats->kernel_seconds = ksum * 1e-3;
@@ -1121,13 +1161,16 @@ int run_batched(int32_t count, const ooc_gemm_desc* d, size_t budget, const ooc_
         for (auto& x : th) x.join();
     }
     int E = 0;
-    int64_t nkern = 0;
+    int64_t nkern = 0, nsplit = 0;
     double flops = 0;
     for (int g = 0; g < count; ++g) {
         if (d[g].M == 0 || d[g].N == 0) continue;
         if (prc[g]) return fail(prc[g], "batched problem " + std::to_string(g) + ": " + pwhy[g]);
         E = std::max(E, n_events(plans[g]));
-        for (const Op& op : sched[g]) nkern += op.kind == kKernel;
+        for (const Op& op : sched[g]) {
+            nkern += op.kind == kKernel;
+            nsplit += op.kind == kSplit;
+        }
         flops += 2.0 * (double)d[g].M * d[g].N * d[g].K;
     }
 
@@ -1159,6 +1202,8 @@ int run_batched(int32_t count, const ooc_gemm_desc* d, size_t budget, const ooc_
     x.kmid.resize(nkern, nullptr);
     for (auto& e : x.kmid) CK(cudaEventCreate(&e));
     x.kmid_set.assign(nkern, 0);
+    x.sev.resize(2 * nsplit, nullptr);
+    for (auto& e : x.sev) CK(cudaEventCreate(&e));
     CK(cudaEventCreate(&x.t_begin));
     for (auto& e : x.t_end) CK(cudaEventCreate(&e));
     const int ev_done0 = 2 * E, ev_fork = 2 * E + 2;
@@ -1189,8 +1234,8 @@ int run_batched(int32_t count, const ooc_gemm_desc* d, size_t budget, const ooc_
             CK(cudaStreamWaitEvent(x.smap[kStreamH2D], x.ev[ev_done0 + h], 0));
             CK(cudaStreamWaitEvent(x.smap[kStreamCompute], x.ev[ev_done0 + h], 0));
         }
-        x.gen.assign(plans[g].slots(), 0);
-        x.split_gen.assign(plans[g].slots(), -1);
+        x.gen.assign(plans[g].slots() + 4, 0);
+        x.split_gen.assign(plans[g].slots() + 4, -1);
         Operands o{d[g].A, d[g].lda, d[g].B, d[g].ldb, d[g].C, d[g].ldc, d[g].alpha, d[g].beta};
         rc = issue_ops(x, plans[g], sched[g], o, 8, inj, why);
         if (rc) {
@@ -1250,6 +1295,11 @@ int run_batched(int32_t count, const ooc_gemm_desc* d, size_t budget, const ooc_
                 CK(cudaEventElapsedTime(&ms, x.kev[2 * k], x.kmid[k]));
                 ssum += ms;
             }
+        }
+        for (long k = 0; x.time_kernels && 2 * k + 1 < (long)x.sev.size() && k < x.n_split; ++k) {
+            CK(cudaEventElapsedTime(&ms, x.sev[2 * k], x.sev[2 * k + 1]));
+            ksum += ms;
+            ssum += ms;
         }
         stats->device_seconds = best * 1e-3;
         stats->kernel_seconds = ksum * 1e-3;  // 0 in graph mode (not timed)

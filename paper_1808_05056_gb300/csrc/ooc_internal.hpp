@@ -54,11 +54,21 @@ struct Plan {
     // Whole-K B slices of the next block column are copied ahead, in row ranges
     // between the A loads of the current column (schedule generator, plan.cpp)
     bool b_prefetch = true;
+    // Split forms: A and B loads land in raw staging areas (nSA for A, nSB for B,
+    // used in turn), and a split op on the compute stream turns the staged data
+    // into the bf16 planes of the operand's slot; the slots hold planes only
+    // (layout in plan.cpp).  Two A areas let the next block's A copy run while
+    // the current one waits for its split; one B area suffices when each whole-K
+    // B slice is loaded once per block column.
+    bool staged = false;
+    int32_t nSA = 0, nSB = 0;
 
     int64_t rows_of(int64_t i) const { return (i + 1) * mb <= M ? mb : M - i * mb; }
     int64_t cols_of(int64_t j) const { return (j + 1) * nb <= N ? nb : N - j * nb; }
     int64_t k_of(int64_t c) const { return (c + 1) * kb <= K ? kb : K - c * kb; }
     int32_t slots() const { return nA + nB + nC + nR; }
+    // staged plans: staging area k of operand mat (kMatA, kMatB) as a slot id past the slots
+    int32_t stage_slot(int mat, int k) const { return slots() + 2 * mat + k; }
     // 0: block (i, j) holds no updated element (skipped); 1: all of it is
     // updated; 2: it straddles the edge of the updated part (masked epilogue,
     // and the block is loaded so that its other elements go back unchanged)
@@ -109,7 +119,7 @@ bool costmodel_get(std::vector<float>& params);
 void costmodel_set(const float* params, int64_t n);
 
 // -------------------------------------------------------------- schedule --
-enum OpKind { kH2D = 0, kKernel = 1, kD2H = 2, kRecord = 3, kWait = 4 };
+enum OpKind { kH2D = 0, kKernel = 1, kD2H = 2, kRecord = 3, kWait = 4, kSplit = 5 };
 enum StreamId { kStreamH2D = 0, kStreamCompute = 1, kStreamD2H = 2 };
 enum MatId { kMatA = 0, kMatB = 1, kMatC = 2 };
 
@@ -134,12 +144,16 @@ struct Op {
 };
 
 // Events: ready(s) after a load into slot s, free(s) after a kernel read s,
-// out(s) after the D2H of C slot s, done(s) after the last kernel of C slot s.
+// out(s) after the D2H of C slot s, done(s) after the last kernel of C slot s;
+// staged plans: sready(a) after a load into staging area a (a = stage_slot id),
+// staged(a) after the split that emptied it.
 inline int32_t ev_ready(const Plan&, int32_t s) { return s; }
 inline int32_t ev_free(const Plan& p, int32_t s) { return p.slots() + s; }
 inline int32_t ev_out(const Plan& p, int32_t s) { return 2 * p.slots() + s; }
 inline int32_t ev_done(const Plan& p, int32_t s) { return 3 * p.slots() + s; }
-inline int32_t n_events(const Plan& p) { return 4 * p.slots(); }
+inline int32_t ev_staged(const Plan& p, int32_t a) { return 4 * p.slots() + (a - p.slots()); }
+inline int32_t ev_sready(const Plan& p, int32_t a) { return 4 * p.slots() + 4 + (a - p.slots()); }
+inline int32_t n_events(const Plan& p) { return 4 * p.slots() + 8; }
 
 void build_schedule(const Plan& plan, std::vector<Op>& ops);
 

@@ -46,6 +46,7 @@ struct FormModel {
     int ctas_per_sm;
     int products;            // slice products per logical product
     int slices;
+    double overlap_cost;     // share of the hidden copy time a step still loses (measured)
 };
 
 FormModel form_model(int form, int es, int64_t K, int slices_opt)
@@ -54,16 +55,23 @@ FormModel form_model(int form, int es, int64_t K, int slices_opt)
     if (form == OOC_FORM_FP64) {
         f.tile_m = 64; f.tile_n = 64; f.rate = 1.0e12; f.ctas_per_sm = 3;
         f.products = 1; f.slices = 1;
+        // no measurable cost: 32768^3 with 180 GB of copies (0.85 s at the link rate) ran 64.16 s
+        // steps on 64.13 s of kernels
+        f.overlap_cost = 0.0;
     } else if (form == OOC_FORM_BF16X3) {
         // measured bf16 rate of the tensor-core kernel on whole-K blocks (1.42-1.64 PFLOP/s)
         f.tile_m = 128; f.tile_n = 128; f.ctas_per_sm = 1;
         f.products = 6; f.slices = 3;
         f.rate = 1.4e15 / 6.0;
+        // copies beside tensor-core kernels share HBM and the power budget: 65536^3 with 309 GB
+        // H2D (1.46 s at the link rate) ran 2.84 s steps on 2.45 s of kernel-stream time
+        f.overlap_cost = 0.27;
     } else {  // Ozaki (measured 1.39-1.40 PFLOP/s bf16)
         int s = slices_opt > 0 ? slices_opt : kOzakiSlicesGemm;
         f.tile_m = 128; f.tile_n = 128; f.ctas_per_sm = 1;
         f.slices = s; f.products = s * (s + 1) / 2;
         f.rate = 1.38e15 / f.products;
+        f.overlap_cost = 0.27;
     }
     (void)es; (void)K;
     return f;
@@ -107,8 +115,17 @@ void layout(Plan& p, const FormModel& f)
         p.b_aux = split_aux_bytes(p, p.nb);
     }
     (void)f;
-    p.device_bytes = p.header + (size_t)p.nA * (p.a_slot + p.a_aux) + (size_t)p.nB * (p.b_slot + p.b_aux) +
-                     (size_t)(p.nC + p.nR) * (p.c_slot + p.c_aux);
+    // split forms keep raw staging areas (two for A; one for B when whole-K B slices are
+    // loaded once per block column, else two) and planes per slot
+    p.staged = p.form != OOC_FORM_FP64;
+    p.nSA = p.staged ? 2 : 0;
+    p.nSB = p.staged ? (p.nkc <= 1 ? 1 : 2) : 0;
+    if (p.staged)
+        p.device_bytes = p.header + (size_t)p.nSA * p.a_slot + (size_t)p.nA * p.a_aux + (size_t)p.nSB * p.b_slot +
+                         (size_t)p.nB * p.b_aux + (size_t)(p.nC + p.nR) * (p.c_slot + p.c_aux);
+    else
+        p.device_bytes = p.header + (size_t)p.nA * (p.a_slot + p.a_aux) + (size_t)p.nB * (p.b_slot + p.b_aux) +
+                         (size_t)(p.nC + p.nR) * (p.c_slot + p.c_aux);
 }
 
 // The updated blocks of block column j: block rows [lo, hi) are updated, of
@@ -248,7 +265,10 @@ double estimate(const Plan& p, const FormModel& f, int sms, double h2d_gbps, dou
     const double fill = ((double)p.mb * p.kb + (double)p.kb * p.nb * std::min<int64_t>(p.nkc, p.nB)) * es / bw_h;
     const double drain = (double)p.mb * p.nb * es / bw_d;
     double bubbles = 0;
-    if (p.nB < 2 * p.nkc && p.nkc <= p.nB) bubbles = (double)(p.w - 1) * p.K * p.nb * es / bw_h;
+    // one B slot: each column switch waits for the next slice, unless a staged plan streams it
+    // into the staging area during the previous column (the B prefetch)
+    const bool staged_prefetch = p.staged && p.b_prefetch && p.nkc == 1 && p.h >= 2;
+    if (p.nB < 2 * p.nkc && p.nkc <= p.nB && !staged_prefetch) bubbles = (double)(p.w - 1) * p.K * p.nb * es / bw_h;
     const double steps = (double)active_blocks(p) * p.nkc;
     // Strided host copies with short rows (< 64 KiB) run far below the link
     // rate on this host link and were seen to slow down further as more host
@@ -268,7 +288,8 @@ double estimate(const Plan& p, const FormModel& f, int sms, double h2d_gbps, dou
     if (narrow_rows(p, kMatA)) narrow += a_loads;
     if (narrow_rows(p, kMatB)) narrow += b_loads;
     if (narrow_rows(p, kMatC)) narrow += c_moved;
-    return std::max(t_comp, t_link) + fill + drain + bubbles + steps * 8e-6 + narrow / (0.25 * bw_h);
+    return std::max(t_comp, t_link) + f.overlap_cost * std::min(t_comp, t_link) + fill + drain + bubbles +
+           steps * 8e-6 + narrow / (0.25 * bw_h);
 }
 
 bool paper_plan(const PlanRequest& rq, Plan& best, std::string& why)
@@ -529,22 +550,43 @@ void plan_features(const Plan& p, const PlanRequest& rq, float* f)
     f[15] = (float)(std::log2(std::max(p.est_seconds, 1e-9)) / 10.0);
 }
 
+// Arena: header, resident C slots (sessions), the A ring, the B ring, the C
+// ring.  Each A / B slot is its raw data then its split scratch; in a staged
+// plan the ring is its raw staging areas then the slots' scratch (planes) only,
+// and a slot's raw data is the first staging area (the schedule names the
+// staging areas by their own ids).
+namespace {
+size_t ring_a_offset(const Plan& p) { return p.header + (size_t)p.nR * (p.c_slot + p.c_aux); }
+size_t ring_b_offset(const Plan& p)
+{
+    return ring_a_offset(p) +
+           (p.staged ? (size_t)p.nSA * p.a_slot + (size_t)p.nA * p.a_aux : (size_t)p.nA * (p.a_slot + p.a_aux));
+}
+size_t ring_c_offset(const Plan& p)
+{
+    return ring_b_offset(p) +
+           (p.staged ? (size_t)p.nSB * p.b_slot + (size_t)p.nB * p.b_aux : (size_t)p.nB * (p.b_slot + p.b_aux));
+}
+}  // namespace
+
 size_t slot_offset(const Plan& p, int32_t s)
 {
     const int32_t ring = p.nA + p.nB + p.nC;
+    if (s >= p.slots()) {  // staging areas: two per operand at most
+        const int a = s - p.slots();
+        return a < 2 ? ring_a_offset(p) + (size_t)a * p.a_slot : ring_b_offset(p) + (size_t)(a - 2) * p.b_slot;
+    }
     if (s >= ring) return p.header + (size_t)(s - ring) * (p.c_slot + p.c_aux);  // resident C slots come first
-    size_t off = p.header + (size_t)p.nR * (p.c_slot + p.c_aux);
-    if (s < p.nA) return off + (size_t)s * (p.a_slot + p.a_aux);
-    off += (size_t)p.nA * (p.a_slot + p.a_aux);
-    s -= p.nA;
-    if (s < p.nB) return off + (size_t)s * (p.b_slot + p.b_aux);
-    off += (size_t)p.nB * (p.b_slot + p.b_aux);
-    s -= p.nB;
-    return off + (size_t)s * (p.c_slot + p.c_aux);
+    if (s < p.nA) return ring_a_offset(p) + (p.staged ? 0 : (size_t)s * (p.a_slot + p.a_aux));
+    if (s < p.nA + p.nB) return ring_b_offset(p) + (p.staged ? 0 : (size_t)(s - p.nA) * (p.b_slot + p.b_aux));
+    return ring_c_offset(p) + (size_t)(s - p.nA - p.nB) * (p.c_slot + p.c_aux);
 }
 
 size_t slot_aux_offset(const Plan& p, int32_t s)
 {
+    if (p.staged && s < p.nA) return ring_a_offset(p) + (size_t)p.nSA * p.a_slot + (size_t)s * p.a_aux;
+    if (p.staged && s < p.nA + p.nB)
+        return ring_b_offset(p) + (size_t)p.nSB * p.b_slot + (size_t)(s - p.nA) * p.b_aux;
     const size_t base = slot_offset(p, s);
     if (s < p.nA) return base + p.a_slot;
     if (s < p.nA + p.nB) return base + p.b_slot;
@@ -585,7 +627,7 @@ struct Gen {
     void push(const Op& o)
     {
         ops.push_back(o);
-        if (o.kind == kH2D || o.kind == kKernel || o.kind == kD2H) ++pos[o.stream];  // work, not markers
+        if (o.kind == kH2D || o.kind == kKernel || o.kind == kD2H || o.kind == kSplit) ++pos[o.stream];  // work
     }
     void emit_wait(int stream, int ev)
     {
@@ -598,6 +640,22 @@ struct Gen {
     {
         Op o; o.kind = kRecord; o.stream = stream; o.event = ev; push(o);
         rec[ev] = {stream, pos[stream]};
+    }
+
+    // Staged plans: what each staging area holds and whether it is still to be
+    // split (a prefetched B slice waits there for its column); the areas of an
+    // operand are used in turn.
+    Tag stage_tag[4];
+    bool stage_pending[4] = {false, false, false, false};
+    int stage_next[2] = {0, 0};
+    int pf_area = -1;
+
+    int next_area(int mat)
+    {
+        const int n = mat == kMatA ? p.nSA : p.nSB;
+        const int a = p.stage_slot(mat, stage_next[mat]);
+        stage_next[mat] = (stage_next[mat] + 1) % n;
+        return a;
     }
 
     int ensure(int mat, const Tag& tg, int64_t t, int lo, int n, int64_t i, int64_t j, int64_t kc)
@@ -615,6 +673,39 @@ struct Gen {
             victim = lo;
             for (int s = lo + 1; s < lo + n; ++s)
                 if (last_use[s] < last_use[victim]) victim = s;
+        }
+        if (p.staged) {
+            // the raw data goes to a staging area once the area's previous content is split;
+            // the split writes the victim's planes on the compute stream, after the victim's
+            // earlier readers there
+            int area = -1;
+            for (int k = 0; k < (mat == kMatA ? p.nSA : p.nSB); ++k) {
+                const int a = p.stage_slot(mat, k);
+                if (stage_pending[a - p.slots()] && stage_tag[a - p.slots()] == tg) area = a;
+            }
+            if (area < 0) {
+                area = next_area(mat);
+                emit_wait(kStreamH2D, ev_staged(p, area));
+                Op o; o.kind = kH2D; o.stream = kStreamH2D; o.wslot = area; o.wtag = tg;
+                o.i = i; o.j = j; o.kc = kc;
+                push(o);
+                emit_record(kStreamH2D, ev_sready(p, area));
+                stage_tag[area - p.slots()] = tg;
+                stage_pending[area - p.slots()] = true;
+            }
+            emit_wait(kStreamCompute, ev_sready(p, area));
+            Op sp; sp.kind = kSplit; sp.stream = kStreamCompute; sp.nr = 1;
+            sp.rslot[0] = area; sp.rtag[0] = tg;
+            sp.wslot = victim; sp.wtag = tg;
+            sp.i = i; sp.j = j; sp.kc = kc;
+            push(sp);
+            emit_record(kStreamCompute, ev_staged(p, area));
+            stage_pending[area - p.slots()] = false;
+            content[victim] = tg;
+            last_use[victim] = t;
+            read_since_load[victim] = false;
+            compute_synced[victim] = true;
+            return victim;
         }
         if (read_since_load[victim]) emit_wait(kStreamH2D, ev_free(p, victim));
         Op o; o.kind = kH2D; o.stream = kStreamH2D; o.wslot = victim; o.wtag = tg;
@@ -634,6 +725,19 @@ struct Gen {
     int pf_slot = -1;
     void prefetch_piece(const Tag& tg, int part, int nparts, int64_t t, int64_t jn)
     {
+        if (p.staged) {  // into a staging area, once the slice it last held has been split
+            if (part == 0) {
+                pf_area = next_area(kMatB);
+                emit_wait(kStreamH2D, ev_staged(p, pf_area));
+            }
+            Op o; o.kind = kH2D; o.stream = kStreamH2D; o.wslot = pf_area; o.wtag = tg;
+            o.i = 0; o.j = jn; o.kc = 0; o.part = part; o.nparts = nparts;
+            push(o);
+            emit_record(kStreamH2D, ev_sready(p, pf_area));
+            stage_tag[pf_area - p.slots()] = tg;
+            stage_pending[pf_area - p.slots()] = true;
+            return;
+        }
         const int lo = p.nA, n = p.nB;
         if (part == 0) {
             int victim = -1;
@@ -675,7 +779,8 @@ struct Gen {
             // copied in row ranges after the A loads of this column's 2nd, 3rd, ... updated blocks,
             // so the column switch finds it resident instead of waiting for the whole slice
             const int64_t ublk = updated_blocks(j);
-            const int npieces = (p.b_prefetch && have_k && p.nkc == 1 && p.nB >= 2 && j + 1 < p.w && ublk >= 2 &&
+            const int npieces = (p.b_prefetch && have_k && p.nkc == 1 && (p.nB >= 2 || p.staged) && j + 1 < p.w &&
+                                 ublk >= 2 &&
                                  updated_blocks(j + 1) > 0)
                                     ? (int)std::min<int64_t>(kMaxPieces, ublk - 1)
                                     : 0;
@@ -737,7 +842,7 @@ struct Gen {
                     push(k);
                     content[sc] = k.wtag;
                     for (int s : {sa, sb}) {
-                        if (s < 0) continue;
+                        if (s < 0 || p.staged) continue;  // staged slots are rewritten on this stream only
                         read_since_load[s] = true;
                         emit_record(kStreamCompute, ev_free(p, s));
                     }

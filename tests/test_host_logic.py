@@ -174,7 +174,7 @@ def test_budget_too_small():
 
 def to_checker(ops):
     """Library schedule entries -> the oracle checker's operation dicts."""
-    kinds = {0: "h2d", 1: "kernel", 2: "d2h", 3: "record", 4: "wait"}
+    kinds = {0: "h2d", 1: "kernel", 2: "d2h", 3: "record", 4: "wait", 5: "split"}
     out = []
     for o in ops:
         d = dict(kind=kinds[o["kind"]], stream=o["stream"])
@@ -210,6 +210,14 @@ CASES = [
     # prefetched in row ranges between this column's A loads
     (1000, 700, 300, 8, 1, 0, dict(mb=128, nb=128, kb=300, depth=2, c_buffers=2, b_buffers=2)),
     (1024, 1024, 512, 4, 1, 0, dict(form=3, mb=256, nb=256, depth=3, b_buffers=2)),
+    # split forms (staged: raw A / B chunks land in one staging area per operand and are split from
+    # there into the slots' planes): one B slot with the next slice streamed into the staging area,
+    # K chunks, ragged edges, Ozaki and BF16x3
+    (1000, 700, 300, 4, 1, 0, dict(form=3, mb=128, nb=128, kb=300, depth=2, c_buffers=2, b_buffers=1)),
+    (1000, 700, 300, 8, 0, 0, dict(form=2, mb=256, nb=128, kb=300, depth=2, c_buffers=2, b_buffers=1)),
+    (600, 520, 700, 8, 1, 0, dict(form=2, mb=128, nb=256, kb=256, depth=2, c_buffers=2, b_buffers=2)),
+    (600, 520, 700, 4, 0, 0, dict(form=3, mb=256, nb=128, kb=192, depth=3, c_buffers=3, b_buffers=1)),
+    (65536, 65536, 65536, 4, 1, 8 << 30, dict(form=3)),
 ]
 
 
@@ -264,6 +272,83 @@ def test_issued_schedule_respects_the_hazard_rule(case):
             assert (0, i, kc, 0) in tags and (1, kc, j, 0) in tags
         if kc > 0 or beta:
             assert (2, i, j, kc) in tags
+
+
+@pytest.mark.parametrize("form,es,b_buffers", [(3, 4, 1), (2, 8, 2)])
+def test_staged_schedule_splits_each_load_once_and_every_wait_is_needed(form, es, b_buffers):
+    """Split forms: every A / B copy writes the operand's staging area (slot ids just past the
+    plan's slots), every such datum is split exactly once into a slot before a kernel reads it,
+    and removing any wait the library issues breaks the hazard rule."""
+    M, N, K = 1000, 700, 300
+    opts = P.make_opts(form=form, mb=128, nb=128, kb=300, depth=2, c_buffers=2, b_buffers=b_buffers)
+    ops = P.ooc_schedule(M, N, K, es, 1, 1 << 40, opts)
+    plan = P.ooc_plan(M, N, K, es, 1, 1 << 40, opts)
+    nslots = plan["depth"] + plan["b_buffers"] + plan["c_buffers"]
+    staged_copies, splits = [], []
+    for o in ops:
+        if o["kind"] == 0 and o["write_tag"][0] in (0, 1):
+            assert o["write_slot"] - nslots - 2 * o["write_tag"][0] in (0, 1)
+            staged_copies.append(tuple(o["write_tag"]))
+        elif o["kind"] == 5:
+            assert o["stream"] == 1 and o["read_slot"][0] - nslots - 2 * o["read_tag"][0][0] in (0, 1)
+            assert tuple(o["read_tag"][0]) == tuple(o["write_tag"]) and o["write_slot"] < nslots
+            splits.append(tuple(o["write_tag"]))
+    # per operand, the staged data in copy order (the row-range pieces of one B slice collapse to
+    # one) is exactly the split order
+    for m in (0, 1):
+        copies = [t for t in staged_copies if t[0] == m]
+        collapsed = [t for k, t in enumerate(copies) if k == 0 or copies[k - 1] != t]
+        assert collapsed == [t for t in splits if t[0] == m] and collapsed
+    chk = to_checker(ops)
+    assert pipeline.check(chk) == []
+    waits = [k for k, o in enumerate(chk) if o["kind"] == "wait"]
+    assert waits
+    assert all(pipeline.check(chk[:k] + chk[k + 1:]) for k in waits)
+
+
+@pytest.mark.parametrize("form,es", [(3, 4), (2, 8)])
+def test_staged_a_loads_run_a_block_ahead(form, es):
+    """Split forms: an A copy waits only for the split of the A chunk two blocks back (two staging
+    areas), so the copy for block i + 1 overlaps kernel i and the kernel before it."""
+    M, N, K = 2000, 700, 300
+    opts = P.make_opts(form=form, mb=128, nb=128, kb=300, depth=2, c_buffers=2, b_buffers=1)
+    ops = P.ooc_schedule(M, N, K, es, 1, 1 << 40, opts)
+    kernels_issued, recorded_after, pending = 0, {}, None
+    checked = 0
+    for o in ops:
+        if o["kind"] == 1:
+            kernels_issued += 1
+        elif o["kind"] == 3 and o["stream"] == 1:
+            recorded_after[o["event"]] = kernels_issued
+        elif o["kind"] == 4 and o["stream"] == 0:
+            pending = o["event"]
+        elif o["kind"] == 0:
+            if pending is not None and o["write_tag"][0] == 0 and pending in recorded_after:
+                assert recorded_after[pending] <= kernels_issued - 2, (o["write_tag"], kernels_issued)
+                checked += 1
+            pending = None
+    assert checked > 10
+
+
+def test_staged_plan_streams_the_next_b_slice_with_one_b_slot():
+    """One B slot in a split-form plan: the next column's slice is copied in pieces into the
+    staging area while the current column runs, and split into the slot at the column switch."""
+    M, N, K = 1000, 700, 300
+    opts = P.make_opts(form=3, mb=128, nb=128, kb=300, depth=2, c_buffers=2, b_buffers=1)
+    ops = P.ooc_schedule(M, N, K, 4, 1, 1 << 40, opts)
+    h, w = -(-M // 128), -(-N // 128)
+    kernel_pos, b_pieces, b_split = {}, {}, {}
+    for n, o in enumerate(ops):
+        if o["kind"] == 1:
+            kernel_pos.setdefault(o["write_tag"][2], []).append(n)
+        elif o["kind"] == 0 and o["write_tag"][0] == 1:
+            b_pieces.setdefault(o["write_tag"][2], []).append(n)
+        elif o["kind"] == 5 and o["write_tag"][0] == 1:
+            b_split[o["write_tag"][2]] = n
+    for j in range(1, w):
+        assert len(b_pieces[j]) == min(8, h - 1)
+        assert kernel_pos[j - 1][0] < min(b_pieces[j]) and max(b_pieces[j]) < kernel_pos[j - 1][-1]
+        assert kernel_pos[j - 1][-1] < b_split[j] < kernel_pos[j][0]
 
 
 def test_checker_catches_a_dropped_library_wait():
