@@ -81,9 +81,9 @@ NOMINAL_FP64_TF, NOMINAL_BF16_TF = 1.25, 2250.0
 # under profiles/ named for the kernel); reported only when a run uses that plan.
 TRAFFIC = {"fp64-32768": {"plan": (2048, 8192, 8192), "bytes": 2.624778e9 + 135.795456e6,
                           "profile": "profiles/fp64_tile_kernel_traffic_32768.md"},
-           "ozaki-65536": {"plan": (7296, 8192, 16384), "bytes": 70.382537984e9 + 580.819456e6,
+           "ozaki-65536": {"plan": (1024, 21888, 16384), "bytes": 11.501296128e9 + 199.416576e6,
                            "profile": "profiles/tc_terms_kernel_traffic_65536.md"},
-           "bf16x3-65536": {"plan": (1792, 4096, 65536), "bytes": 4.663631360e9 + 29.363200e6,
+           "bf16x3-65536": {"plan": (1024, 7296, 65536), "bytes": 4.110287616e9 + 27.162880e6,
                             "profile": "profiles/tc_terms_kernel_traffic_65536.md"}}
 
 
