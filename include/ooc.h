@@ -91,7 +91,8 @@ typedef struct {
 typedef struct {
     double seconds;          /* host wall time of the call                          */
     double device_seconds;   /* first H2D start to last D2H end (CUDA events)       */
-    double kernel_seconds;   /* summed duration of the tile-contraction launches    */
+    double kernel_seconds;   /* summed duration of the tile-contraction launches
+                                and the split forms' splitting kernels              */
     double tflops;           /* 2*M*N*K / seconds / 1e12 (transfers included)       */
     double h2d_bytes;        /* bytes copied host -> device                          */
     double d2h_bytes;        /* bytes copied device -> host                          */
