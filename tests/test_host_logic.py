@@ -505,3 +505,22 @@ def test_session_call_schedule(case):
                 assert (2, i, j, v - 1) in o["read_tag"]
     if nres == h * w:
         assert plan["c_buffers"] == 0
+
+
+def test_planner_keeps_the_fp64_benchmark_plan():
+    """FP64 32768^3 in 4 GiB: the plan the FP64 tile kernel was measured on (0.996 of its peak);
+    the planner's overlap cost is zero for FP64, so copies hidden under FP64 kernels do not move it."""
+    p = P.ooc_plan(32768, 32768, 32768, 8, 1, 4 << 30, P.make_opts(form=P.OOC_FORM_FP64))
+    assert (p["mb"], p["nb"], p["kb"]) == (2048, 8192, 8192)
+
+
+@pytest.mark.parametrize("form,es,K,beta,budget,max_h2d", [
+    (3, 4, 65536, 1, 8 << 30, 200e9),    # BF16x3 65536^3, 8 GiB: was 309 GB per call before staging
+    (2, 8, 16384, 0, 16 << 30, 40e9),    # Ozaki 65536^2 x 16384, 16 GiB: was 77 GB
+])
+def test_planner_prefers_fewer_bytes_for_the_split_forms(form, es, K, beta, budget, max_h2d):
+    """The split forms' staged layout fits wider blocks in the budget, and the overlap cost makes
+    the planner use that room to send fewer bytes; the plan still fits the budget."""
+    p = P.ooc_plan(65536, 65536, K, es, beta, budget, P.make_opts(form=form))
+    assert p["h2d_bytes"] <= max_h2d
+    assert p["device_bytes"] <= budget
