@@ -372,12 +372,9 @@ struct Exec {
     long n_copy = 0, n_kern = 0;
     std::vector<cudaEvent_t> ev;
     std::vector<cudaEvent_t> kev;  // timing pairs around tile kernels
-    std::vector<cudaEvent_t> kmid;  // split forms: between a tile's split kernels and its contraction
-    std::vector<char> kmid_set;
     std::vector<cudaEvent_t> sev;   // staged plans: timing pairs around split ops
     long n_split = 0;
     std::vector<TraceRec> trace;
-    std::vector<int64_t> gen, split_gen;  // loads into each slot / loads already split (split forms)
     int64_t launches = 0;                 // kernels launched by this call
     cudaEvent_t t_begin = nullptr, t_end[3] = {nullptr, nullptr, nullptr};
 
@@ -392,7 +389,6 @@ struct Exec {
             if (s) cudaStreamSynchronize(s);
         for (auto& e : ev) { if (e) cudaEventDestroy(e); e = nullptr; }
         for (auto& e : kev) { if (e) cudaEventDestroy(e); e = nullptr; }
-        for (auto& e : kmid) { if (e) cudaEventDestroy(e); e = nullptr; }
         for (auto& e : sev) { if (e) cudaEventDestroy(e); e = nullptr; }
         for (auto& r : trace) { if (r.e0) cudaEventDestroy(r.e0); if (r.e1) cudaEventDestroy(r.e1); }
         trace.clear();
@@ -449,16 +445,21 @@ int split_slot(const Plan& p, Exec& x, int src_slot, int dst_slot, bool is_a, in
                                planes, st, why);
 }
 
+// A tile of a split form: the contraction of the slots' planes (written by the
+// schedule's split ops; split-form plans are always staged) into C slot sc.
 int launch_split_tile(const Plan& p, const Op& op, Exec& x, const Operands& o, int sa, int sb, int sc,
                       std::string& why)
 {
+    if (!p.staged) {
+        why = "split-form plan without staging areas";
+        return OOC_ERR_INVALID_ARG;
+    }
     const bool ozaki = p.form == OOC_FORM_OZAKI;
     const int S = split_planes(p);
     const int64_t rows = p.rows_of(op.i), cols = p.cols_of(op.j), K = p.K > 0 ? p.k_of(op.kc) : 0;  // this chunk
     const int64_t k_pad = split_k_pad(p);
     const int64_t ra_pad = split_rows_pad(p.mb), rb_pad = split_rows_pad(p.nb);
     int* err = reinterpret_cast<int*>(x.arena);
-    void* st = x.smap[kStreamCompute];
     struct Side {
         int slot;
         bool is_a;
@@ -471,18 +472,6 @@ int launch_split_tile(const Plan& p, const Op& op, Exec& x, const Operands& o, i
         char* aux = x.base + slot_aux_offset(p, s);
         planes[q] = aux;
         exps[q] = reinterpret_cast<int*>(aux + split_planes_bytes(p, sides[q].is_a ? p.mb : p.nb));
-        // staged plans split in their own schedule ops; otherwise the first tile after a load splits it
-        if (p.staged || x.split_gen[s] == x.gen[s]) continue;
-        const int rc = split_slot(p, x, s, s, sides[q].is_a, sides[q].is_a ? rows : cols, K, why);
-        if (rc) return rc;
-        x.split_gen[s] = x.gen[s];
-    }
-    if (x.time_kernels && x.n_kern < (long)x.kmid.size()) {
-        if (cudaEventRecord(x.kmid[x.n_kern], static_cast<cudaStream_t>(st)) != cudaSuccess) {
-            why = "split timing event";
-            return OOC_ERR_CUDA;
-        }
-        x.kmid_set[x.n_kern] = 1;
     }
     TcProblem P;
     P.M = rows; P.N = cols; P.k_pad = K > 0 ? k_pad : 0;
@@ -515,7 +504,7 @@ int launch_split_tile(const Plan& p, const Op& op, Exec& x, const Operands& o, i
         P.tri_off = p.block_off(op.i, op.j);
     }
     ++x.launches;
-    return launch_tc_terms(P, st, why);
+    return launch_tc_terms(P, x.smap[kStreamCompute], why);
 }
 
 int launch_tile(const Plan& p, const Op& op, Exec& x, const Operands& o, std::string& why)
@@ -576,7 +565,6 @@ int issue_ops(Exec& x, const Plan& p, const std::vector<Op>& ops, const Operands
             if (inj.copy >= 0 && x.n_copy++ == inj.copy) return fail(OOC_ERR_INJECTED, "injected copy failure");
             const Tag& t = op.wtag;
             char* dst = x.base + slot_offset(p, op.wslot);
-            ++x.gen[op.wslot];
             const char* src;
             int64_t rows, width, spitch, dpitch;
             if (t.m == kMatA) {
@@ -661,8 +649,6 @@ int execute(Exec& x, const std::vector<Op>& ops, const Operands& o, int es, cons
     const Plan& p = x.p;
     std::string why;
     int rc = OOC_OK;
-    x.gen.assign(p.slots() + 4, 0);  // + the staging areas of staged plans
-    x.split_gen.assign(p.slots() + 4, -1);
     x.ev.resize(n_events(p), nullptr);
     for (auto& e : x.ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     int64_t nkern = 0, nsplit = 0;
@@ -672,9 +658,6 @@ int execute(Exec& x, const std::vector<Op>& ops, const Operands& o, int es, cons
     }
     x.kev.resize(2 * nkern, nullptr);
     for (auto& e : x.kev) CK(cudaEventCreate(&e));
-    x.kmid.resize(nkern, nullptr);
-    for (auto& e : x.kmid) CK(cudaEventCreate(&e));
-    x.kmid_set.assign(nkern, 0);
     x.sev.resize(2 * nsplit, nullptr);
     for (auto& e : x.sev) CK(cudaEventCreate(&e));
     CK(cudaEventCreate(&x.t_begin));
@@ -726,10 +709,6 @@ int execute(Exec& x, const std::vector<Op>& ops, const Operands& o, int es, cons
         for (int64_t k = 0; k < x.n_kern; ++k) {
             CK(cudaEventElapsedTime(&ms, x.kev[2 * k], x.kev[2 * k + 1]));
             ksum += ms;
-            if (x.kmid_set[k]) {
-                CK(cudaEventElapsedTime(&ms, x.kev[2 * k], x.kmid[k]));
-                ssum += ms;
-            }
         }
         for (long k = 0; 2 * k + 1 < (long)x.sev.size() && k < x.n_split; ++k) {
             CK(cudaEventElapsedTime(&ms, x.sev[2 * k], x.sev[2 * k + 1]));
@@ -1199,9 +1178,6 @@ int run_batched(int32_t count, const ooc_gemm_desc* d, size_t budget, const ooc_
     for (auto& e : x.ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     x.kev.resize(2 * nkern, nullptr);
     for (auto& e : x.kev) CK(cudaEventCreate(&e));
-    x.kmid.resize(nkern, nullptr);
-    for (auto& e : x.kmid) CK(cudaEventCreate(&e));
-    x.kmid_set.assign(nkern, 0);
     x.sev.resize(2 * nsplit, nullptr);
     for (auto& e : x.sev) CK(cudaEventCreate(&e));
     CK(cudaEventCreate(&x.t_begin));
@@ -1234,8 +1210,6 @@ int run_batched(int32_t count, const ooc_gemm_desc* d, size_t budget, const ooc_
             CK(cudaStreamWaitEvent(x.smap[kStreamH2D], x.ev[ev_done0 + h], 0));
             CK(cudaStreamWaitEvent(x.smap[kStreamCompute], x.ev[ev_done0 + h], 0));
         }
-        x.gen.assign(plans[g].slots() + 4, 0);
-        x.split_gen.assign(plans[g].slots() + 4, -1);
         Operands o{d[g].A, d[g].lda, d[g].B, d[g].ldb, d[g].C, d[g].ldc, d[g].alpha, d[g].beta};
         rc = issue_ops(x, plans[g], sched[g], o, 8, inj, why);
         if (rc) {
@@ -1291,10 +1265,6 @@ int run_batched(int32_t count, const ooc_gemm_desc* d, size_t budget, const ooc_
         for (int64_t k = 0; x.time_kernels && k < x.n_kern; ++k) {
             CK(cudaEventElapsedTime(&ms, x.kev[2 * k], x.kev[2 * k + 1]));
             ksum += ms;
-            if (x.kmid_set[k]) {
-                CK(cudaEventElapsedTime(&ms, x.kev[2 * k], x.kmid[k]));
-                ssum += ms;
-            }
         }
         for (long k = 0; x.time_kernels && 2 * k + 1 < (long)x.sev.size() && k < x.n_split; ++k) {
             CK(cudaEventElapsedTime(&ms, x.sev[2 * k], x.sev[2 * k + 1]));
